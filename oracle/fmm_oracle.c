@@ -1,0 +1,249 @@
+/*
+ * FP64 CPU oracle for FusedMM: an SDDMM feeding an SpMM.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference leg of bench.py may load or run this code; the
+ * product library (libfmm) never calls it, and the two share no source,
+ * header, helper or table.
+ *
+ * Every routine is the plain definition written out as loops, in FP64, with
+ * the inner product summed over k in ascending order and the nonzeros of a
+ * row visited in CSR order.  No blocking, no reordering, no fusion beyond
+ * what the definition itself states.
+ *
+ * Sparse S is given as CSR with 64-bit row pointers and column indices:
+ *   rowptr[m+1], colidx[nnz], vals[nnz] (vals == NULL means every s_ij = 1).
+ * Dense matrices are row-major: A is m x r, B is n x r, G is m x r (or n x r).
+ * Duplicate (i, j) entries are allowed and each one contributes; columns of a
+ * row need not be sorted.
+ *
+ * Each routine returns 0, or -1 if an index is outside its matrix (the
+ * outputs are then unspecified).
+ *
+ * Paper passages followed (Bharadwaj, Buluc, Demmel, "Distributed-Memory
+ * Sparse Kernels for Machine Learning"):
+ *   Sec. II, Eq. (1)        SDDMM(A, B, S) = S * (A B^T), only at nonzeros of S
+ *   Sec. II                 SpMMA(S, B) = S B,  SpMMB(S, A) = S^T A,
+ *                           FusedMMA = SpMMA(SDDMM(A,B,S), B),
+ *                           FusedMMB = SpMMB(SDDMM(A,B,S), A)
+ *   Sec. IV-A               per-nonzero SpMMA update A_i += S_ij B_j
+ *   Sec. IV-B               row form FusedMMA_i = sum_j S_ij <A_i, B_j> B_j
+ * The gradients are not in the paper; they are the derivatives of the
+ * scalar L = <G, FusedMM(S, A, B)> with respect to A, B and the values of S,
+ * on a fixed pattern.
+ *
+ * Built as a shared library by oracle/build.py:
+ *   gcc -O2 -fopenmp -fPIC -shared -o oracle/_build/liboracle.so oracle/fmm_oracle.c
+ * Rows are independent in the row-wise routines, so those loop over rows with
+ * an OpenMP parallel-for; the scatter routines run sequentially.
+ */
+#include <stdint.h>
+#include <string.h>
+
+static double oracle_s(const double *vals, int64_t p)
+{
+    return vals ? vals[p] : 1.0;
+}
+
+/* <x, y> = sum_{k < r} x[k] * y[k], k ascending. */
+static double oracle_dot(const double *x, const double *y, int64_t r)
+{
+    double acc = 0.0;
+    for (int64_t k = 0; k < r; ++k)
+        acc += x[k] * y[k];
+    return acc;
+}
+
+static int oracle_check(int64_t m, int64_t n, const int64_t *rowptr,
+                        const int64_t *colidx)
+{
+    if (m < 0 || n < 0 || rowptr[0] != 0)
+        return -1;
+    for (int64_t i = 0; i < m; ++i) {
+        if (rowptr[i + 1] < rowptr[i])
+            return -1;
+        for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p)
+            if (colidx[p] < 0 || colidx[p] >= n)
+                return -1;
+    }
+    return 0;
+}
+
+/* SDDMM, Sec. II Eq. (1): v[p] = s_ij * <A_i, B_j> for the p-th nonzero (i, j). */
+int oracle_sddmm(int64_t m, int64_t n, int64_t r, const int64_t *rowptr,
+                 const int64_t *colidx, const double *vals, const double *A,
+                 const double *B, double *v)
+{
+    if (oracle_check(m, n, rowptr, colidx))
+        return -1;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < m; ++i)
+        for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+            int64_t j = colidx[p];
+            v[p] = oracle_s(vals, p) * oracle_dot(A + i * r, B + j * r, r);
+        }
+    return 0;
+}
+
+/* SpMMA, Sec. II and the update of Sec. IV-A: out_i = sum_p v[p] * B_j. */
+int oracle_spmm(int64_t m, int64_t n, int64_t r, const int64_t *rowptr,
+                const int64_t *colidx, const double *v, const double *B,
+                double *out)
+{
+    if (oracle_check(m, n, rowptr, colidx))
+        return -1;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < m; ++i) {
+        double *o = out + i * r;
+        for (int64_t k = 0; k < r; ++k)
+            o[k] = 0.0;
+        for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+            const double *b = B + colidx[p] * r;
+            for (int64_t k = 0; k < r; ++k)
+                o[k] += v[p] * b[k];
+        }
+    }
+    return 0;
+}
+
+/* SpMMB, Sec. II: out = S^T A, i.e. out_j += v[p] * A_i for each nonzero
+ * (i, j), scattered straight from the CSR of S (no transposed copy). */
+int oracle_spmm_t(int64_t m, int64_t n, int64_t r, const int64_t *rowptr,
+                  const int64_t *colidx, const double *v, const double *A,
+                  double *out)
+{
+    if (oracle_check(m, n, rowptr, colidx))
+        return -1;
+    memset(out, 0, (size_t)(n * r) * sizeof(double));
+    for (int64_t i = 0; i < m; ++i)
+        for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+            double *o = out + colidx[p] * r;
+            const double *a = A + i * r;
+            for (int64_t k = 0; k < r; ++k)
+                o[k] += v[p] * a[k];
+        }
+    return 0;
+}
+
+/* FusedMMA, Sec. II and its row form in Sec. IV-B:
+ * out_i = sum_{(i,j) in nnz(S)} s_ij <A_i, B_j> B_j.
+ * The SDDMM value of each nonzero is held in one scalar and used at once. */
+int oracle_fusedmm(int64_t m, int64_t n, int64_t r, const int64_t *rowptr,
+                   const int64_t *colidx, const double *vals, const double *A,
+                   const double *B, double *out)
+{
+    if (oracle_check(m, n, rowptr, colidx))
+        return -1;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < m; ++i) {
+        double *o = out + i * r;
+        for (int64_t k = 0; k < r; ++k)
+            o[k] = 0.0;
+        for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+            const double *b = B + colidx[p] * r;
+            double v = oracle_s(vals, p) * oracle_dot(A + i * r, b, r);
+            for (int64_t k = 0; k < r; ++k)
+                o[k] += v * b[k];
+        }
+    }
+    return 0;
+}
+
+/* FusedMMB, Sec. II: out = S'^T A with S' = SDDMM(A, B, S), i.e.
+ * out_j = sum_{(i,j) in nnz(S)} s_ij <A_i, B_j> A_i.
+ * Scattered directly over the CSR of S; deliberately builds no S^T. */
+int oracle_fusedmm_t(int64_t m, int64_t n, int64_t r, const int64_t *rowptr,
+                     const int64_t *colidx, const double *vals, const double *A,
+                     const double *B, double *out)
+{
+    if (oracle_check(m, n, rowptr, colidx))
+        return -1;
+    memset(out, 0, (size_t)(n * r) * sizeof(double));
+    for (int64_t i = 0; i < m; ++i) {
+        const double *a = A + i * r;
+        for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+            int64_t j = colidx[p];
+            double v = oracle_s(vals, p) * oracle_dot(a, B + j * r, r);
+            double *o = out + j * r;
+            for (int64_t k = 0; k < r; ++k)
+                o[k] += v * a[k];
+        }
+    }
+    return 0;
+}
+
+/* Gradient of L = sum_i <G_i, FusedMMA(S, A, B)_i> (G is m x r).
+ * With d = <A_i, B_j> and w = <G_i, B_j> at nonzero p = (i, j):
+ *   ds[p] = d * w
+ *   dA_i  = sum_p s_ij * w * B_j
+ *   dB_j  = sum_p s_ij * (d * G_i + w * A_i)
+ * Any of dA, dB, ds may be NULL.  Sequential (dB is a scatter). */
+int oracle_fusedmm_grad(int64_t m, int64_t n, int64_t r, const int64_t *rowptr,
+                        const int64_t *colidx, const double *vals,
+                        const double *A, const double *B, const double *G,
+                        double *dA, double *dB, double *ds)
+{
+    if (oracle_check(m, n, rowptr, colidx))
+        return -1;
+    if (dA)
+        memset(dA, 0, (size_t)(m * r) * sizeof(double));
+    if (dB)
+        memset(dB, 0, (size_t)(n * r) * sizeof(double));
+    for (int64_t i = 0; i < m; ++i) {
+        const double *a = A + i * r, *g = G + i * r;
+        for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+            int64_t j = colidx[p];
+            const double *b = B + j * r;
+            double s = oracle_s(vals, p);
+            double d = oracle_dot(a, b, r);
+            double w = oracle_dot(g, b, r);
+            if (ds)
+                ds[p] = d * w;
+            if (dA)
+                for (int64_t k = 0; k < r; ++k)
+                    dA[i * r + k] += s * w * b[k];
+            if (dB)
+                for (int64_t k = 0; k < r; ++k)
+                    dB[j * r + k] += s * (d * g[k] + w * a[k]);
+        }
+    }
+    return 0;
+}
+
+/* Gradient of L = sum_j <Gn_j, FusedMMB(S, A, B)_j> (Gn is n x r).
+ * With d = <A_i, B_j> and w = <Gn_j, A_i> at nonzero p = (i, j):
+ *   ds[p] = d * w
+ *   dB_j  = sum_p s_ij * w * A_i
+ *   dA_i  = sum_p s_ij * (d * Gn_j + w * B_j)
+ * Any of dA, dB, ds may be NULL.  Sequential. */
+int oracle_fusedmm_t_grad(int64_t m, int64_t n, int64_t r,
+                          const int64_t *rowptr, const int64_t *colidx,
+                          const double *vals, const double *A, const double *B,
+                          const double *Gn, double *dA, double *dB, double *ds)
+{
+    if (oracle_check(m, n, rowptr, colidx))
+        return -1;
+    if (dA)
+        memset(dA, 0, (size_t)(m * r) * sizeof(double));
+    if (dB)
+        memset(dB, 0, (size_t)(n * r) * sizeof(double));
+    for (int64_t i = 0; i < m; ++i) {
+        const double *a = A + i * r;
+        for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+            int64_t j = colidx[p];
+            const double *b = B + j * r, *g = Gn + j * r;
+            double s = oracle_s(vals, p);
+            double d = oracle_dot(a, b, r);
+            double w = oracle_dot(g, a, r);
+            if (ds)
+                ds[p] = d * w;
+            if (dB)
+                for (int64_t k = 0; k < r; ++k)
+                    dB[j * r + k] += s * w * a[k];
+            if (dA)
+                for (int64_t k = 0; k < r; ++k)
+                    dA[i * r + k] += s * (d * g[k] + w * b[k]);
+        }
+    }
+    return 0;
+}
