@@ -1,0 +1,222 @@
+/*
+ * fmm.h -- C ABI of libfmm: FusedMM (an SDDMM feeding an SpMM) on one GPU.
+ *
+ * Operations (Bharadwaj, Buluc, Demmel, "Distributed-Memory Sparse Kernels
+ * for Machine Learning", Sec. II):
+ *   SDDMM(A, B, S)  = S * (A B^T), computed only at the nonzeros of S  (Eq. 1)
+ *   SpMMA(S, B)     = S B          SpMMB(S, A) = S^T A
+ *   FusedMMA(S,A,B) = SpMMA(SDDMM(A, B, S), B)
+ *                   : out_i = sum_{(i,j) in nnz(S)} s_ij <A_i, B_j> B_j    (Sec. IV-B)
+ *   FusedMMB(S,A,B) = SpMMB(SDDMM(A, B, S), A)
+ *                   : out_j = sum_{(i,j) in nnz(S)} s_ij <A_i, B_j> A_i
+ * FusedMMB is computed from a transposed copy of the pattern, as the paper
+ * does by interchanging A and B and using S^T (Sec. IV-B, last paragraph).
+ * The fused kernels keep each SDDMM value in registers, so the intermediate
+ * sparse matrix never reaches memory (local kernel fusion, Sec. IV-B (2)).
+ *
+ * Shapes and layout
+ *   S      m x n sparse, CSR: row_ptr[m+1] and col_idx[nnz], int32, on the
+ *          device.  row_ptr[0] = 0, row_ptr is nondecreasing, row_ptr[m] = nnz,
+ *          0 <= col_idx[p] < n.  Duplicate (i, j) entries are allowed and each
+ *          one contributes; columns need not be sorted within a row.
+ *   vals   nnz float32 values of S in CSR order, on the device; NULL means
+ *          every value is 1.  Values are read on every call, so they may
+ *          change between calls on one plan; the pattern may not.
+ *   A      m x r, B n x r: dense, row-major, contiguous, on the device, of the
+ *          plan's dtype (FMM_F32 = float32, FMM_BF16 = bfloat16 bits).
+ *   G, Gn  gradient of a scalar loss with respect to the FusedMMA output
+ *          (m x r) or FusedMMB output (n x r): float32, row-major.
+ *   out, v, dA, dB, ds: float32, row-major, on the device, caller-owned, and
+ *          overwritten (never accumulated into).  Every row of an output is
+ *          written, empty rows with zeros.
+ * Arithmetic is float32 with float32 accumulation; bfloat16 inputs are
+ * widened exactly to float32.  Results are deterministic: the same plan and
+ * inputs give bitwise identical outputs on every call (no floating-point
+ * atomics).  16-byte aligned dense pointers with r in {32, 64, 128, 256}
+ * take the vectorised kernels; any other r or alignment takes a slower
+ * generic GPU kernel with the same results up to rounding.  No call ever
+ * falls back to the CPU.
+ *
+ * Streams and ownership
+ *   Every compute call is asynchronous on the given stream (a cudaStream_t;
+ *   NULL is the legacy default stream) and returns once its kernels are
+ *   queued.  The caller owns every buffer it passes and must keep the pattern
+ *   (row_ptr, col_idx) alive and unchanged for the life of the plan.  A plan
+ *   owns its own device workspace (transposed pattern, schedules, partial
+ *   rows of split rows), allocated by fmm_plan_create and freed by
+ *   fmm_plan_destroy; compute calls allocate nothing.  Calls on one plan
+ *   share that workspace and must be ordered (one stream, or synchronised).
+ *
+ * Errors
+ *   Every entry point returns FMM_OK (0) or a negative status; see
+ *   fmm_status_string().  Invalid arguments are reported before anything is
+ *   queued.  FMM_ECUDA reports a CUDA runtime error seen while queueing.
+ */
+#ifndef FMM_H
+#define FMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t (same underlying type); NULL is the legacy default stream. */
+typedef struct CUstream_st *fmm_stream;
+
+enum fmm_status {
+    FMM_OK = 0,
+    FMM_EINVAL = -1,        /* NULL pointer, negative size, malformed CSR   */
+    FMM_EUNSUPPORTED = -2,  /* unknown dtype, r < 1, or a missing S^T       */
+    FMM_EOVERFLOW = -3,     /* nnz >= 2^31 or a size that overflows         */
+    FMM_ECUDA = -4,         /* CUDA runtime error (launch, copy, device)    */
+    FMM_ENOMEM = -5         /* device allocation failed (plan creation)     */
+};
+
+enum fmm_dtype {
+    FMM_F32 = 0,            /* float32 dense inputs                          */
+    FMM_BF16 = 1            /* bfloat16 dense inputs, float32 accumulation   */
+};
+
+/* fmm_plan_options.flags */
+#define FMM_PLAN_NO_TRANSPOSE 1u  /* skip S^T: the _t and _bwd calls are then FMM_EUNSUPPORTED */
+
+/* Sparse pattern S (device pointers; not copied, referenced by the plan). */
+typedef struct fmm_csr {
+    int32_t m;                /* rows of S                                */
+    int32_t n;                /* columns of S                             */
+    int64_t nnz;              /* nonzeros, must be < 2^31                 */
+    const int32_t *row_ptr;   /* m + 1 entries                            */
+    const int32_t *col_idx;   /* nnz entries                              */
+} fmm_csr;
+
+/* Plan options; pass NULL to fmm_plan_create for the defaults. */
+typedef struct fmm_plan_options {
+    uint32_t flags;           /* FMM_PLAN_* bits                          */
+    int32_t split_nnz;        /* rows (and columns, for S^T) with more
+                                 nonzeros than this are split into chunks of
+                                 this many nonzeros whose partial rows are
+                                 summed in a fixed order; 0 = default (512)  */
+    int32_t unroll;           /* nonzeros in flight per row group in the
+                                 vectorised kernels: 0 = default, or 2, 4, 8 */
+} fmm_plan_options;
+
+typedef struct fmm_plan fmm_plan;   /* opaque */
+
+typedef struct fmm_plan_info {
+    int32_t m, n, r, dtype;
+    int64_t nnz;
+    int32_t max_row_nnz;      /* longest row of S                          */
+    int32_t max_col_nnz;      /* longest column of S (-1 without S^T)      */
+    int32_t split_rows;       /* rows of S split into chunks               */
+    int32_t split_cols;       /* columns of S split into chunks            */
+    int32_t row_chunks;       /* chunks over the split rows                */
+    int32_t col_chunks;       /* chunks over the split columns             */
+    int32_t split_nnz;        /* chunk size in nonzeros                    */
+    int32_t unroll;           /* nonzeros in flight per row group          */
+    int64_t workspace_bytes;  /* device bytes owned by the plan            */
+} fmm_plan_info;
+
+/*
+ * Checks a CSR pattern on the device (row_ptr[0] = 0, nondecreasing,
+ * row_ptr[m] = nnz, 0 <= col_idx < n).  Synchronises the stream.
+ * *first_bad (may be NULL) receives -1 if the pattern is valid, else the
+ * smallest offending index: a row_ptr position p as -(p + 2), or a col_idx
+ * position p as p.  Returns FMM_OK or FMM_EINVAL (malformed) or an error.
+ */
+int fmm_csr_validate(const fmm_csr *S, fmm_stream stream, int64_t *first_bad);
+
+/*
+ * One-time preprocessing of a pattern, amortised over repeated calls with
+ * the same pattern and possibly different values (Sec. I; Sec. III-A on
+ * preprocessing amortised by repeated kernel calls).  Validates S (as
+ * fmm_csr_validate), builds S^T as CSR with a permutation back to the CSR
+ * slots of S (the "two copies, one transposed" of Sec. IV-B), orders rows and
+ * columns by length and splits the longest ones into chunks.  r >= 1 is the
+ * dense width and dtype an fmm_dtype.  Synchronises the stream; allocates
+ * device memory.  *plan receives the plan (NULL on error).
+ */
+int fmm_plan_create(const fmm_csr *S, int32_t r, int32_t dtype,
+                    const fmm_plan_options *options, fmm_stream stream,
+                    fmm_plan **plan);
+
+/* Frees a plan and its workspace (synchronises the device first).  NULL is a
+ * no-op. */
+int fmm_plan_destroy(fmm_plan *plan);
+
+/* Copies the plan's sizes and schedule summary into *info. */
+int fmm_plan_get_info(const fmm_plan *plan, fmm_plan_info *info);
+
+/*
+ * SDDMM, Sec. II Eq. (1):  v[p] = s_ij * <A_i, B_j>  for the p-th nonzero
+ * (i, j) of S in CSR order.  v_out: nnz float32.
+ */
+int fmm_sddmm(const fmm_plan *plan, const float *vals, const void *A,
+              const void *B, float *v_out, fmm_stream stream);
+
+/*
+ * SpMMA, Sec. II:  out_i = sum_p v[p] * B_j.  v: nnz float32 in CSR order of
+ * S (e.g. the output of fmm_sddmm).  out_m: m x r float32.
+ */
+int fmm_spmm(const fmm_plan *plan, const float *v, const void *B,
+             float *out_m, fmm_stream stream);
+
+/*
+ * SpMMB, Sec. II:  out_j = sum_p v[p] * A_i  (S^T A), gathered through S^T.
+ * v: nnz float32 in CSR order of S.  out_n: n x r float32.
+ */
+int fmm_spmm_t(const fmm_plan *plan, const float *v, const void *A,
+               float *out_n, fmm_stream stream);
+
+/*
+ * FusedMMA, Sec. II and Sec. IV-B:  out_i = sum_j s_ij <A_i, B_j> B_j, one
+ * fused kernel (the SDDMM value of a nonzero stays in registers).
+ * out_m: m x r float32.
+ */
+int fmm_fusedmm(const fmm_plan *plan, const float *vals, const void *A,
+                const void *B, float *out_m, fmm_stream stream);
+
+/*
+ * FusedMMB, Sec. II:  out_j = sum_i s_ij <A_i, B_j> A_i, computed as
+ * FusedMMA over S^T with A and B interchanged (Sec. IV-B).  out_n: n x r.
+ */
+int fmm_fusedmm_t(const fmm_plan *plan, const float *vals, const void *A,
+                  const void *B, float *out_n, fmm_stream stream);
+
+/*
+ * Adjoint of FusedMMA (not in the paper): gradients of L = <G, FusedMMA>
+ * with d = <A_i, B_j>, w = <G_i, B_j> recomputed per nonzero:
+ *   ds[p] = d * w,  dA_i = sum_p s_ij w B_j,  dB_j = sum_p s_ij (d G_i + w A_i).
+ * G: m x r float32.  dA (m x r), dB (n x r), ds (nnz, CSR order): float32;
+ * any of them may be NULL to skip it.  The SDDMM values are never stored.
+ */
+int fmm_fusedmm_bwd(const fmm_plan *plan, const float *vals, const void *A,
+                    const void *B, const float *G, float *dA, float *dB,
+                    float *ds, fmm_stream stream);
+
+/*
+ * Adjoint of FusedMMB: gradients of L = <Gn, FusedMMB> with
+ * d = <A_i, B_j>, w = <Gn_j, A_i>:
+ *   ds[p] = d * w,  dB_j = sum_p s_ij w A_i,  dA_i = sum_p s_ij (d Gn_j + w B_j).
+ * Gn: n x r float32.  dA, dB, ds as for fmm_fusedmm_bwd.
+ */
+int fmm_fusedmm_t_bwd(const fmm_plan *plan, const float *vals, const void *A,
+                      const void *B, const float *Gn, float *dA, float *dB,
+                      float *ds, fmm_stream stream);
+
+/* Static description of a status code (never NULL). */
+const char *fmm_status_string(int status);
+
+/* Message of the last error seen by this thread's calls ("" if none). */
+const char *fmm_last_error(void);
+
+/* ABI version of this header: (major << 16) | minor. */
+int32_t fmm_version(void);
+
+#define FMM_VERSION ((1 << 16) | 0)
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FMM_H */

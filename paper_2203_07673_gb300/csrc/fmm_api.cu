@@ -1,0 +1,283 @@
+// C-ABI entry points of libfmm (declared in include/fmm.h).
+#include <cstdint>
+#include <cstdio>
+
+#include "fmm_internal.cuh"
+
+namespace fmm {
+
+bool fast_r(int32_t r) { return r == 32 || r == 64 || r == 128 || r == 256; }
+
+static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+cudaError_t launch_pass(int mode, int dtype, int unroll, const PassArgs &a, cudaStream_t st)
+{
+    const bool vec = fast_r(a.r) && aligned16(a.L) && aligned16(a.Y) && aligned16(a.H) &&
+                     aligned16(a.out) && aligned16(a.partials);
+    if (dtype == FMM_BF16)
+        return launch_pass_bf16(mode, unroll, vec, a, st);
+    return launch_pass_f32(mode, unroll, vec, a, st);
+}
+
+}  // namespace fmm
+
+using namespace fmm;
+
+namespace {
+
+int check_plan(const fmm_plan *p)
+{
+    if (!p) {
+        set_error_msg("plan is NULL");
+        return FMM_EINVAL;
+    }
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        set_error("cudaGetDevice", e);
+        return FMM_ECUDA;
+    }
+    if (dev != p->device) {
+        set_error_msg("current device differs from the plan's device");
+        return FMM_EINVAL;
+    }
+    return FMM_OK;
+}
+
+// A dense operand with `rows` rows may be NULL only when it has no rows.
+int need(const void *ptr, int64_t rows, const char *name)
+{
+    if (!ptr && rows > 0) {
+        char msg[96];
+        snprintf(msg, sizeof(msg), "%s is NULL", name);
+        set_error_msg(msg);
+        return FMM_EINVAL;
+    }
+    return FMM_OK;
+}
+
+int need_t(const fmm_plan *p)
+{
+    if (!p->has_t) {
+        set_error_msg("plan built with FMM_PLAN_NO_TRANSPOSE");
+        return FMM_EUNSUPPORTED;
+    }
+    return FMM_OK;
+}
+
+int run_pass(const fmm_plan *p, const Side &side, int mode, const float *s, const void *L,
+             const void *Y, const float *H, float *out, float *nzout, cudaStream_t st)
+{
+    PassArgs a;
+    a.row_ptr = side.row_ptr;
+    a.col_idx = side.col_idx;
+    a.perm = side.perm;
+    a.order = side.light_order();
+    a.n_light = side.n_light;
+    a.chunks = side.chunks;
+    a.n_chunks = side.n_chunks;
+    a.partials = side.partials;
+    a.s = s;
+    a.L = L;
+    a.Y = Y;
+    a.H = H;
+    a.out = out;
+    a.nzout = nzout;
+    a.r = p->r;
+    cudaError_t e = launch_pass(mode, p->dtype, p->unroll, a, st);
+    if (e == cudaSuccess && mode != M_SDDMM)
+        e = launch_combine(side, out, p->r, st);
+    if (e != cudaSuccess) {
+        set_error("kernel launch", e);
+        return FMM_ECUDA;
+    }
+    return FMM_OK;
+}
+
+#define CHECK(x)              \
+    do {                      \
+        int _rc = (x);        \
+        if (_rc) return _rc;  \
+    } while (0)
+
+}  // namespace
+
+extern "C" {
+
+int fmm_csr_validate(const fmm_csr *S, fmm_stream stream, int64_t *first_bad)
+{
+    if (first_bad) *first_bad = -1;
+    CHECK(check_csr_args(S));
+    return validate_csr(S, (cudaStream_t)stream, first_bad);
+}
+
+int fmm_plan_create(const fmm_csr *S, int32_t r, int32_t dtype, const fmm_plan_options *options,
+                    fmm_stream stream, fmm_plan **plan)
+{
+    if (!plan) {
+        set_error_msg("plan output pointer is NULL");
+        return FMM_EINVAL;
+    }
+    *plan = nullptr;
+    CHECK(check_csr_args(S));
+    if (r < 1) {
+        set_error_msg("r must be >= 1");
+        return FMM_EUNSUPPORTED;
+    }
+    if (dtype != FMM_F32 && dtype != FMM_BF16) {
+        set_error_msg("unknown dtype");
+        return FMM_EUNSUPPORTED;
+    }
+    if ((int64_t)std::max(S->m, S->n) * r >= (int64_t(1) << 40)) {
+        set_error_msg("dense operand too large");
+        return FMM_EOVERFLOW;
+    }
+    if (options) {
+        if (options->split_nnz < 0 ||
+            (options->unroll != 0 && options->unroll != 2 && options->unroll != 4 &&
+             options->unroll != 8) ||
+            (options->flags & ~FMM_PLAN_NO_TRANSPOSE)) {
+            set_error_msg("invalid plan options");
+            return FMM_EINVAL;
+        }
+    }
+    CHECK(validate_csr(S, (cudaStream_t)stream, nullptr));
+    return create_plan(S, r, dtype, options, (cudaStream_t)stream, plan);
+}
+
+int fmm_plan_destroy(fmm_plan *plan)
+{
+    destroy_plan(plan);
+    return FMM_OK;
+}
+
+int fmm_plan_get_info(const fmm_plan *p, fmm_plan_info *info)
+{
+    if (!p || !info) {
+        set_error_msg("NULL argument");
+        return FMM_EINVAL;
+    }
+    info->m = p->m;
+    info->n = p->n;
+    info->r = p->r;
+    info->dtype = p->dtype;
+    info->nnz = p->nnz;
+    info->max_row_nnz = p->rows.max_nnz;
+    info->max_col_nnz = p->has_t ? p->cols.max_nnz : -1;
+    info->split_rows = p->rows.n_split;
+    info->split_cols = p->cols.n_split;
+    info->row_chunks = p->rows.n_chunks;
+    info->col_chunks = p->cols.n_chunks;
+    info->split_nnz = p->split_nnz;
+    info->unroll = p->unroll;
+    info->workspace_bytes = p->workspace_bytes;
+    return FMM_OK;
+}
+
+int fmm_sddmm(const fmm_plan *p, const float *vals, const void *A, const void *B, float *v_out,
+              fmm_stream stream)
+{
+    CHECK(check_plan(p));
+    CHECK(need(A, p->m, "A"));
+    CHECK(need(B, p->n, "B"));
+    CHECK(need(v_out, p->nnz, "v_out"));
+    return run_pass(p, p->rows, M_SDDMM, vals, A, B, nullptr, nullptr, v_out,
+                    (cudaStream_t)stream);
+}
+
+int fmm_spmm(const fmm_plan *p, const float *v, const void *B, float *out_m, fmm_stream stream)
+{
+    CHECK(check_plan(p));
+    CHECK(need(v, p->nnz, "v"));
+    CHECK(need(B, p->n, "B"));
+    CHECK(need(out_m, p->m, "out_m"));
+    return run_pass(p, p->rows, M_SPMM, v, nullptr, B, nullptr, out_m, nullptr,
+                    (cudaStream_t)stream);
+}
+
+int fmm_spmm_t(const fmm_plan *p, const float *v, const void *A, float *out_n, fmm_stream stream)
+{
+    CHECK(check_plan(p));
+    CHECK(need_t(p));
+    CHECK(need(v, p->nnz, "v"));
+    CHECK(need(A, p->m, "A"));
+    CHECK(need(out_n, p->n, "out_n"));
+    return run_pass(p, p->cols, M_SPMM, v, nullptr, A, nullptr, out_n, nullptr,
+                    (cudaStream_t)stream);
+}
+
+int fmm_fusedmm(const fmm_plan *p, const float *vals, const void *A, const void *B, float *out_m,
+                fmm_stream stream)
+{
+    CHECK(check_plan(p));
+    CHECK(need(A, p->m, "A"));
+    CHECK(need(B, p->n, "B"));
+    CHECK(need(out_m, p->m, "out_m"));
+    return run_pass(p, p->rows, M_FUSED, vals, A, B, nullptr, out_m, nullptr,
+                    (cudaStream_t)stream);
+}
+
+int fmm_fusedmm_t(const fmm_plan *p, const float *vals, const void *A, const void *B,
+                  float *out_n, fmm_stream stream)
+{
+    CHECK(check_plan(p));
+    CHECK(need_t(p));
+    CHECK(need(A, p->m, "A"));
+    CHECK(need(B, p->n, "B"));
+    CHECK(need(out_n, p->n, "out_n"));
+    return run_pass(p, p->cols, M_FUSED, vals, B, A, nullptr, out_n, nullptr,
+                    (cudaStream_t)stream);
+}
+
+int fmm_fusedmm_bwd(const fmm_plan *p, const float *vals, const void *A, const void *B,
+                    const float *G, float *dA, float *dB, float *ds, fmm_stream stream)
+{
+    CHECK(check_plan(p));
+    CHECK(need(A, p->m, "A"));
+    CHECK(need(B, p->n, "B"));
+    CHECK(need(G, p->m, "G"));
+    if (dB)
+        CHECK(need_t(p));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (dA || ds)
+        CHECK(run_pass(p, p->rows, M_BWD_ROW, vals, A, B, G, dA, ds, st));
+    if (dB)
+        CHECK(run_pass(p, p->cols, M_BWD_COL, vals, B, A, G, dB, nullptr, st));
+    return FMM_OK;
+}
+
+int fmm_fusedmm_t_bwd(const fmm_plan *p, const float *vals, const void *A, const void *B,
+                      const float *Gn, float *dA, float *dB, float *ds, fmm_stream stream)
+{
+    CHECK(check_plan(p));
+    CHECK(need(A, p->m, "A"));
+    CHECK(need(B, p->n, "B"));
+    CHECK(need(Gn, p->n, "Gn"));
+    if (dB || ds)
+        CHECK(need_t(p));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (dB || ds)
+        CHECK(run_pass(p, p->cols, M_BWD_ROW, vals, B, A, Gn, dB, ds, st));
+    if (dA)
+        CHECK(run_pass(p, p->rows, M_BWD_COL, vals, A, B, Gn, dA, nullptr, st));
+    return FMM_OK;
+}
+
+const char *fmm_status_string(int status)
+{
+    switch (status) {
+    case FMM_OK: return "ok";
+    case FMM_EINVAL: return "invalid argument";
+    case FMM_EUNSUPPORTED: return "unsupported";
+    case FMM_EOVERFLOW: return "size overflow";
+    case FMM_ECUDA: return "CUDA error";
+    case FMM_ENOMEM: return "out of device memory";
+    default: return "unknown status";
+    }
+}
+
+const char *fmm_last_error(void) { return last_error(); }
+
+int32_t fmm_version(void) { return FMM_VERSION; }
+
+}  // extern "C"

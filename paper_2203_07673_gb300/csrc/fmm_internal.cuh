@@ -1,0 +1,100 @@
+// Internal declarations shared by the libfmm translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fmm.h"
+
+namespace fmm {
+
+// One side of a plan: the CSR that a row pass walks (S itself, or S^T with a
+// permutation back to the CSR slots of S) plus its schedule.
+struct Side {
+    int32_t rows = 0;                 // rows of this CSR (m for S, n for S^T)
+    const int32_t *row_ptr = nullptr; // rows + 1
+    const int32_t *col_idx = nullptr; // nnz
+    const int32_t *perm = nullptr;    // nnz; NULL on the S side (identity)
+    int32_t *order = nullptr;         // rows: split rows first, then the rest
+                                      // by decreasing length (ties by index)
+    int32_t n_split = 0;              // rows split into chunks
+    int32_t n_light = 0;              // rows - n_split
+    int4 *chunks = nullptr;           // {row, begin, end, unused} per chunk
+    int32_t n_chunks = 0;
+    int4 *split = nullptr;            // {row, first chunk, chunk count, unused}
+    float *partials = nullptr;        // n_chunks x r partial rows
+    int32_t max_nnz = 0;              // longest row
+    const int32_t *light_order() const { return order ? order + n_split : nullptr; }
+};
+
+// Kernel roles.  "local" rows belong to the row being produced; "gathered"
+// rows are fetched per nonzero through col_idx.
+enum Mode : int {
+    M_FUSED = 0,    // acc += s * <L_i, Y_j> * Y_j
+    M_SDDMM = 1,    // nzout[p] = s * <L_i, Y_j>
+    M_SPMM = 2,     // acc += s * Y_j            (s = the SDDMM values)
+    M_BWD_ROW = 3,  // d = <L_i,Y_j>, w = <H_i,Y_j>: nzout[p] = d w, acc += s w Y_j
+    M_BWD_COL = 4   // d = <Y_i,L_j>, w = <H_i,L_j>: acc += s (d H_i + w Y_i)
+};
+
+struct PassArgs {
+    // pattern walked
+    const int32_t *row_ptr;
+    const int32_t *col_idx;
+    const int32_t *perm;       // maps a slot of this CSR to the CSR slot of S
+    const int32_t *order;      // light rows in processing order
+    int32_t n_light;
+    const int4 *chunks;
+    int32_t n_chunks;
+    float *partials;
+    // operands
+    const float *s;            // per-nonzero scalars in S order (NULL = 1)
+    const void *L;             // local rows (dtype of the plan)
+    const void *Y;             // gathered rows (dtype of the plan)
+    const float *H;            // float32 gradient rows (local or gathered)
+    float *out;                // rows x r (NULL: not stored)
+    float *nzout;              // per-nonzero output in S order (NULL: none)
+    int32_t r;
+};
+
+// Launches one row pass (main kernel; the combine kernel for split rows is
+// separate).  dtype: FMM_F32 / FMM_BF16.  unroll: 2, 4 or 8.
+cudaError_t launch_pass(int mode, int dtype, int unroll, const PassArgs &a,
+                        cudaStream_t st);
+cudaError_t launch_pass_f32(int mode, int unroll, bool vec, const PassArgs &a,
+                            cudaStream_t st);
+cudaError_t launch_pass_bf16(int mode, int unroll, bool vec, const PassArgs &a,
+                             cudaStream_t st);
+// Sums the partial rows of every split row, in chunk order, into out.
+cudaError_t launch_combine(const Side &side, float *out, int32_t r,
+                           cudaStream_t st);
+
+bool fast_r(int32_t r);
+
+// Plan construction and error reporting (fmm_plan.cu).
+int check_csr_args(const fmm_csr *S);
+int validate_csr(const fmm_csr *S, cudaStream_t st, int64_t *first_bad);
+int create_plan(const fmm_csr *S, int32_t r, int32_t dtype, const fmm_plan_options *opt,
+                cudaStream_t st, fmm_plan **out);
+void destroy_plan(fmm_plan *p);
+void set_error(const char *what, cudaError_t e);
+void set_error_msg(const char *what);
+const char *last_error();
+
+}  // namespace fmm
+
+struct fmm_plan {
+    int32_t m = 0, n = 0, r = 0, dtype = 0;
+    int64_t nnz = 0;
+    uint32_t flags = 0;
+    int32_t split_nnz = 512;
+    int32_t unroll = 0;
+    bool has_t = false;
+    fmm::Side rows;   // S
+    fmm::Side cols;   // S^T
+    int32_t *row_ptr_t = nullptr;
+    int32_t *col_idx_t = nullptr;
+    int32_t *perm_t = nullptr;
+    int64_t workspace_bytes = 0;
+    int device = 0;
+};

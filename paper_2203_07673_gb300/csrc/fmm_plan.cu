@@ -1,0 +1,564 @@
+// Plan construction: validation of the pattern, the transposed pattern with
+// its permutation (stable LSD radix sort by column), and the schedule of each
+// side (rows ordered by length, long rows split into fixed-size chunks).
+//
+// The transposed copy of S is how the paper obtains FusedMMB and SpMMB from
+// the FusedMMA machinery: interchange A and B and use S^T, "storing two
+// copies of the sparse matrix, one with the coordinates transposed"
+// (Sec. IV-B, last paragraph).  Preprocessing the pattern once and reusing it
+// over repeated calls with the same nonzero structure follows Sec. I and
+// Sec. III-A.  All of it runs on the device; the host only sizes buffers and
+// lays out the (few) chunks of split rows.
+#include <algorithm>
+#include <cstdio>
+#include <vector>
+
+#include "fmm_internal.cuh"
+
+namespace fmm {
+
+// ---------------------------------------------------------------- validation
+
+__global__ void validate_kernel(const int32_t *row_ptr, const int32_t *col_idx, int32_t m,
+                                int32_t n, int64_t nnz, unsigned long long *bad_rp,
+                                unsigned long long *bad_ci)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= (int64_t)m; i += stride) {
+        const int64_t v = row_ptr[i];
+        bool bad = v < 0 || v > nnz;
+        if (i == 0 && v != 0) bad = true;
+        if (i == m && v != nnz) bad = true;
+        if (i > 0 && v < (int64_t)row_ptr[i - 1]) bad = true;
+        if (bad)
+            atomicMin(bad_rp, (unsigned long long)i);
+    }
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += stride) {
+        const int32_t c = col_idx[p];
+        if (c < 0 || c >= n)
+            atomicMin(bad_ci, (unsigned long long)p);
+    }
+}
+
+// ------------------------------------------------------------------ scan
+
+// Exclusive prefix sum of n uint32 values (in may equal out), one block of
+// 1024 threads walking the array in tiles of 4096 with a running carry.
+__global__ void __launch_bounds__(1024) scan_exclusive_kernel(const uint32_t *in, uint32_t *out,
+                                                              int64_t n)
+{
+    __shared__ uint32_t warp_tot[32];
+    __shared__ uint32_t carry_s;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (tid == 0)
+        carry_s = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < n; base += 4096) {
+        uint32_t x[4], sum = 0;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int64_t idx = base + tid * 4 + t;
+            x[t] = idx < n ? in[idx] : 0u;
+            sum += x[t];
+        }
+        uint32_t incl = sum;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += y;
+        }
+        if (lane == 31)
+            warp_tot[w] = incl;
+        __syncthreads();
+        if (w == 0) {
+            uint32_t t = warp_tot[lane], ti = t;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, ti, off);
+                if (lane >= off) ti += y;
+            }
+            warp_tot[lane] = ti - t;   // exclusive over warps
+        }
+        __syncthreads();
+        uint32_t run = carry_s + warp_tot[w] + (incl - sum);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int64_t idx = base + tid * 4 + t;
+            if (idx < n)
+                out[idx] = run;
+            run += x[t];
+        }
+        __syncthreads();
+        if (tid == 1023)
+            carry_s = run;
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------ radix sort
+// Stable LSD radix sort of (key, value) pairs, 8-bit digits, tiles of 4096
+// items (256 threads x 16).  Each warp owns 512 consecutive items of a tile
+// and ranks them in order with __match_any_sync, so equal digits keep their
+// input order: the sort is stable and fully deterministic.
+
+constexpr int RS_TILE = 4096;
+
+__global__ void __launch_bounds__(256) rs_hist_kernel(const uint32_t *keys, int64_t n, int shift,
+                                                      uint32_t *ghist, int ntiles)
+{
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    for (int t = 0; t < 16; ++t) {
+        const int64_t idx = base + t * 256 + threadIdx.x;
+        if (idx < n)
+            atomicAdd(&h[(keys[idx] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    ghist[(size_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(256) rs_scatter_kernel(const uint32_t *kin, const int32_t *vin,
+                                                         uint32_t *kout, int32_t *vout, int64_t n,
+                                                         int shift, const uint32_t *goff,
+                                                         int ntiles)
+{
+    __shared__ uint32_t wc[8][256];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int64_t base = (int64_t)blockIdx.x * RS_TILE + w * 512;
+    uint32_t key[16];
+    int32_t val[16];
+    int dig[16];
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+        const int64_t idx = base + t * 32 + lane;
+        if (idx < n) {
+            key[t] = kin[idx];
+            val[t] = vin[idx];
+            dig[t] = (int)((key[t] >> shift) & 255u);
+        } else {
+            key[t] = 0; val[t] = 0; dig[t] = 256;
+        }
+    }
+    for (int i = tid; i < 8 * 256; i += 256)
+        (&wc[0][0])[i] = 0;
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+        const unsigned peers = __match_any_sync(0xffffffffu, dig[t]);
+        const int leader = 31 - __clz(peers);
+        if (dig[t] < 256 && lane == leader)
+            wc[w][dig[t]] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    {
+        uint32_t run = goff[(size_t)tid * ntiles + blockIdx.x];
+        for (int w2 = 0; w2 < 8; ++w2) {
+            const uint32_t c = wc[w2][tid];
+            wc[w2][tid] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+        const unsigned peers = __match_any_sync(0xffffffffu, dig[t]);
+        const int leader = 31 - __clz(peers);
+        if (dig[t] < 256) {
+            const uint32_t pos = wc[w][dig[t]] + __popc(peers & lt);
+            kout[pos] = key[t];
+            vout[pos] = val[t];
+        }
+        __syncwarp();
+        if (dig[t] < 256 && lane == leader)
+            wc[w][dig[t]] += __popc(peers);
+        __syncwarp();
+    }
+}
+
+static int blocks_for(int64_t n, int threads, int cap = 1 << 20)
+{
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    return (int)std::min<int64_t>(b, cap);
+}
+
+// Sorts by the low `bits` bits of the keys; on return *in_b says whether the
+// result sits in (kb, vb) rather than (ka, va).
+static cudaError_t radix_sort(uint32_t *ka, int32_t *va, uint32_t *kb, int32_t *vb, int64_t n,
+                              int bits, uint32_t *ghist, cudaStream_t st, bool *in_b)
+{
+    *in_b = false;
+    if (n <= 1)
+        return cudaSuccess;
+    const int ntiles = (int)((n + RS_TILE - 1) / RS_TILE);
+    uint32_t *ks = ka, *kd = kb;
+    int32_t *vs = va, *vd = vb;
+    for (int shift = 0; shift < bits; shift += 8) {
+        rs_hist_kernel<<<ntiles, 256, 0, st>>>(ks, n, shift, ghist, ntiles);
+        scan_exclusive_kernel<<<1, 1024, 0, st>>>(ghist, ghist, (int64_t)ntiles * 256);
+        rs_scatter_kernel<<<ntiles, 256, 0, st>>>(ks, vs, kd, vd, n, shift, ghist, ntiles);
+        std::swap(ks, kd);
+        std::swap(vs, vd);
+        *in_b = !*in_b;
+    }
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------- side schedule
+
+// Sort key of a row by length: split rows first (0), then decreasing length
+// (lengths >= 254 share key 1), empty rows last (255).
+__global__ void row_keys_kernel(const int32_t *row_ptr, int32_t rows, int32_t split_nnz,
+                                uint32_t *keys, int32_t *vals, int32_t *counters)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += stride) {
+        const int32_t deg = row_ptr[i + 1] - row_ptr[i];
+        uint32_t key;
+        if (deg > split_nnz) {
+            key = 0;
+            atomicAdd(&counters[0], 1);
+        } else if (deg >= 254) {
+            key = 1;
+        } else if (deg == 0) {
+            key = 255;
+        } else {
+            key = 255u - (uint32_t)deg;
+        }
+        atomicMax(&counters[1], deg);
+        keys[i] = key;
+        vals[i] = (int32_t)i;
+    }
+}
+
+__global__ void split_ranges_kernel(const int32_t *order, int32_t n_split, const int32_t *row_ptr,
+                                    int2 *ranges)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_split; i += stride) {
+        const int32_t row = order[i];
+        ranges[i] = make_int2(row_ptr[row], row_ptr[row + 1]);
+    }
+}
+
+// ----------------------------------------------------------- transpose
+
+__global__ void count_cols_kernel(const int32_t *col_idx, int64_t nnz, uint32_t *cnt)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += stride)
+        atomicAdd(&cnt[col_idx[p]], 1u);
+}
+
+__global__ void init_pairs_kernel(const int32_t *col_idx, int64_t nnz, uint32_t *keys,
+                                  int32_t *vals)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += stride) {
+        keys[p] = (uint32_t)col_idx[p];
+        vals[p] = (int32_t)p;
+    }
+}
+
+// col_idx_t[q] = the row of S holding nonzero perm[q] (binary search in row_ptr).
+__global__ void rows_of_kernel(const int32_t *row_ptr, int32_t m, const int32_t *perm,
+                               int32_t *col_idx_t, int64_t nnz)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nnz; q += stride) {
+        const int32_t p = perm[q];
+        int32_t lo = 0, hi = m - 1;
+        while (lo < hi) {
+            const int32_t mid = lo + (hi - lo + 1) / 2;
+            if (row_ptr[mid] <= p) lo = mid; else hi = mid - 1;
+        }
+        col_idx_t[q] = lo;
+    }
+}
+
+}  // namespace fmm
+
+// ====================================================================== API
+
+using namespace fmm;
+
+namespace {
+
+thread_local char g_last_error[256] = "";
+
+struct Temps {
+    uint32_t *ka = nullptr, *kb = nullptr, *ghist = nullptr;
+    int32_t *va = nullptr, *vb = nullptr, *counters = nullptr;
+    ~Temps()
+    {
+        cudaFree(ka); cudaFree(kb); cudaFree(ghist);
+        cudaFree(va); cudaFree(vb); cudaFree(counters);
+    }
+};
+
+}  // namespace
+
+namespace fmm {
+
+void set_error(const char *what, cudaError_t e)
+{
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s", what,
+             e == cudaSuccess ? "ok" : cudaGetErrorString(e));
+}
+
+void set_error_msg(const char *what)
+{
+    snprintf(g_last_error, sizeof(g_last_error), "%s", what);
+}
+
+const char *last_error() { return g_last_error; }
+
+template <typename P>
+static cudaError_t dmalloc(P **p, size_t count, fmm_plan *plan)
+{
+    size_t bytes = count * sizeof(P);
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc((void **)p, bytes);
+    if (e == cudaSuccess && plan) plan->workspace_bytes += (int64_t)bytes;
+    return e;
+}
+
+#define FMM_TRY(expr, what)                                          \
+    do {                                                             \
+        cudaError_t _e = (expr);                                     \
+        if (_e != cudaSuccess) {                                     \
+            set_error(what, _e);                                     \
+            return _e == cudaErrorMemoryAllocation ? FMM_ENOMEM : FMM_ECUDA; \
+        }                                                            \
+    } while (0)
+
+static int build_side(Side &side, const int32_t *row_ptr, int32_t rows, int32_t split_nnz,
+                      int32_t r, Temps &tmp, cudaStream_t st, fmm_plan *plan)
+{
+    side.rows = rows;
+    side.row_ptr = row_ptr;
+    if (rows == 0)
+        return FMM_OK;
+    FMM_TRY(dmalloc(&side.order, (size_t)rows, plan), "allocate row order");
+    FMM_TRY(cudaMemsetAsync(tmp.counters, 0, 2 * sizeof(int32_t), st), "memset");
+    row_keys_kernel<<<blocks_for(rows, 256), 256, 0, st>>>(row_ptr, rows, split_nnz, tmp.ka,
+                                                           tmp.va, tmp.counters);
+    FMM_TRY(cudaGetLastError(), "row keys");
+    bool in_b = false;
+    FMM_TRY(radix_sort(tmp.ka, tmp.va, tmp.kb, tmp.vb, rows, 8, tmp.ghist, st, &in_b),
+            "row order sort");
+    FMM_TRY(cudaMemcpyAsync(side.order, in_b ? tmp.vb : tmp.va, (size_t)rows * sizeof(int32_t),
+                            cudaMemcpyDeviceToDevice, st), "copy row order");
+    int32_t counters[2];
+    FMM_TRY(cudaMemcpyAsync(counters, tmp.counters, sizeof(counters), cudaMemcpyDeviceToHost, st),
+            "read counters");
+    FMM_TRY(cudaStreamSynchronize(st), "plan sync");
+    side.n_split = counters[0];
+    side.max_nnz = counters[1];
+    side.n_light = rows - side.n_split;
+    if (side.n_split == 0)
+        return FMM_OK;
+    int2 *d_ranges = nullptr;
+    FMM_TRY(cudaMalloc(&d_ranges, sizeof(int2) * side.n_split), "allocate ranges");
+    split_ranges_kernel<<<blocks_for(side.n_split, 256), 256, 0, st>>>(side.order, side.n_split,
+                                                                       row_ptr, d_ranges);
+    std::vector<int2> ranges(side.n_split);
+    std::vector<int32_t> rows_h(side.n_split);
+    cudaError_t e = cudaMemcpyAsync(ranges.data(), d_ranges, sizeof(int2) * side.n_split,
+                                    cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(rows_h.data(), side.order, sizeof(int32_t) * side.n_split,
+                            cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(st);
+    cudaFree(d_ranges);
+    FMM_TRY(e, "read split rows");
+    std::vector<int4> chunks, split;
+    for (int32_t s = 0; s < side.n_split; ++s) {
+        const int32_t beg = ranges[s].x, end = ranges[s].y;
+        const int32_t first = (int32_t)chunks.size();
+        for (int64_t c = beg; c < end; c += split_nnz)
+            chunks.push_back(make_int4(rows_h[s], (int32_t)c,
+                                       (int32_t)std::min<int64_t>(end, c + split_nnz), 0));
+        split.push_back(make_int4(rows_h[s], first, (int32_t)chunks.size() - first, 0));
+    }
+    side.n_chunks = (int32_t)chunks.size();
+    FMM_TRY(dmalloc(&side.chunks, chunks.size(), plan), "allocate chunks");
+    FMM_TRY(dmalloc(&side.split, split.size(), plan), "allocate split table");
+    FMM_TRY(dmalloc(&side.partials, (size_t)side.n_chunks * r, plan), "allocate partials");
+    FMM_TRY(cudaMemcpyAsync(side.chunks, chunks.data(), sizeof(int4) * chunks.size(),
+                            cudaMemcpyHostToDevice, st), "upload chunks");
+    FMM_TRY(cudaMemcpyAsync(side.split, split.data(), sizeof(int4) * split.size(),
+                            cudaMemcpyHostToDevice, st), "upload split table");
+    FMM_TRY(cudaStreamSynchronize(st), "plan sync");
+    return FMM_OK;
+}
+
+static void free_side(Side &s)
+{
+    cudaFree(s.order); cudaFree(s.chunks); cudaFree(s.split); cudaFree(s.partials);
+    s = Side();
+}
+
+int check_csr_args(const fmm_csr *S)
+{
+    if (!S) { set_error_msg("S is NULL"); return FMM_EINVAL; }
+    if (S->m < 0 || S->n < 0 || S->nnz < 0) { set_error_msg("negative size"); return FMM_EINVAL; }
+    if (S->nnz >= (int64_t(1) << 31)) { set_error_msg("nnz >= 2^31"); return FMM_EOVERFLOW; }
+    if (!S->row_ptr) { set_error_msg("row_ptr is NULL"); return FMM_EINVAL; }
+    if (S->nnz > 0 && !S->col_idx) { set_error_msg("col_idx is NULL"); return FMM_EINVAL; }
+    return FMM_OK;
+}
+
+int validate_csr(const fmm_csr *S, cudaStream_t st, int64_t *first_bad)
+{
+    if (first_bad) *first_bad = -1;
+    unsigned long long *d_bad = nullptr;
+    FMM_TRY(cudaMalloc(&d_bad, 2 * sizeof(unsigned long long)), "allocate validation flags");
+    const unsigned long long init[2] = {~0ull, ~0ull};
+    unsigned long long bad[2] = {~0ull, ~0ull};
+    cudaError_t e = cudaMemcpyAsync(d_bad, init, sizeof(init), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        const int64_t work = std::max<int64_t>((int64_t)S->m + 1, S->nnz);
+        validate_kernel<<<blocks_for(work, 256, 152 * 16), 256, 0, st>>>(
+            S->row_ptr, S->col_idx, S->m, S->n, S->nnz, d_bad, d_bad + 1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(bad, d_bad, sizeof(bad), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(st);
+    cudaFree(d_bad);
+    FMM_TRY(e, "validate CSR");
+    if (bad[0] != ~0ull) {
+        if (first_bad) *first_bad = -(int64_t)bad[0] - 2;
+        snprintf(g_last_error, sizeof(g_last_error), "malformed CSR: row_ptr[%llu]", bad[0]);
+        return FMM_EINVAL;
+    }
+    if (bad[1] != ~0ull) {
+        if (first_bad) *first_bad = (int64_t)bad[1];
+        snprintf(g_last_error, sizeof(g_last_error), "malformed CSR: col_idx[%llu] out of range",
+                 bad[1]);
+        return FMM_EINVAL;
+    }
+    return FMM_OK;
+}
+
+void destroy_plan(fmm_plan *p)
+{
+    if (!p) return;
+    cudaDeviceSynchronize();
+    free_side(p->rows);
+    free_side(p->cols);
+    cudaFree(p->row_ptr_t);
+    cudaFree(p->col_idx_t);
+    cudaFree(p->perm_t);
+    delete p;
+}
+
+int create_plan(const fmm_csr *S, int32_t r, int32_t dtype, const fmm_plan_options *opt,
+                cudaStream_t st, fmm_plan **out)
+{
+    fmm_plan *p = new fmm_plan();
+    p->m = S->m; p->n = S->n; p->nnz = S->nnz; p->r = r; p->dtype = dtype;
+    p->flags = opt ? opt->flags : 0u;
+    if (opt && opt->split_nnz > 0) p->split_nnz = opt->split_nnz;
+    p->unroll = (opt && opt->unroll > 0) ? opt->unroll : 8;
+    cudaGetDevice(&p->device);
+    Temps tmp;
+    const int64_t N = std::max<int64_t>({(int64_t)S->m, (int64_t)S->n, S->nnz, 1});
+    const int64_t ntiles = (N + RS_TILE - 1) / RS_TILE;
+    int rc = FMM_OK;
+    auto fail = [&](int code) { destroy_plan(p); *out = nullptr; return code; };
+#define PLAN_TRY(expr, what)                                                    \
+    do {                                                                        \
+        cudaError_t _e = (expr);                                                \
+        if (_e != cudaSuccess) {                                                \
+            set_error(what, _e);                                                \
+            return fail(_e == cudaErrorMemoryAllocation ? FMM_ENOMEM : FMM_ECUDA); \
+        }                                                                       \
+    } while (0)
+    PLAN_TRY(dmalloc(&tmp.ka, N, nullptr), "allocate sort keys");
+    PLAN_TRY(dmalloc(&tmp.kb, N, nullptr), "allocate sort keys");
+    PLAN_TRY(dmalloc(&tmp.va, N, nullptr), "allocate sort values");
+    PLAN_TRY(dmalloc(&tmp.vb, N, nullptr), "allocate sort values");
+    PLAN_TRY(dmalloc(&tmp.ghist, (size_t)ntiles * 256, nullptr), "allocate histogram");
+    PLAN_TRY(dmalloc(&tmp.counters, 2, nullptr), "allocate counters");
+
+    rc = build_side(p->rows, S->row_ptr, S->m, p->split_nnz, r, tmp, st, p);
+    if (rc) return fail(rc);
+    p->rows.col_idx = S->col_idx;
+    p->rows.perm = nullptr;
+
+    if (!(p->flags & FMM_PLAN_NO_TRANSPOSE)) {
+        p->has_t = true;
+        PLAN_TRY(dmalloc(&p->row_ptr_t, (size_t)S->n + 1, p), "allocate S^T row_ptr");
+        PLAN_TRY(dmalloc(&p->col_idx_t, (size_t)S->nnz, p), "allocate S^T col_idx");
+        PLAN_TRY(dmalloc(&p->perm_t, (size_t)S->nnz, p), "allocate S^T perm");
+        uint32_t *cnt = reinterpret_cast<uint32_t *>(p->row_ptr_t);
+        PLAN_TRY(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * ((size_t)S->n + 1), st), "memset");
+        if (S->nnz > 0) {
+            count_cols_kernel<<<blocks_for(S->nnz, 256, 152 * 32), 256, 0, st>>>(S->col_idx,
+                                                                                 S->nnz, cnt);
+            init_pairs_kernel<<<blocks_for(S->nnz, 256, 152 * 32), 256, 0, st>>>(
+                S->col_idx, S->nnz, tmp.ka, tmp.va);
+            PLAN_TRY(cudaGetLastError(), "transpose setup");
+        }
+        scan_exclusive_kernel<<<1, 1024, 0, st>>>(cnt, cnt, (int64_t)S->n + 1);
+        PLAN_TRY(cudaGetLastError(), "transpose scan");
+        int bits = 0;
+        while (bits < 31 && (int64_t(1) << bits) < (int64_t)S->n) ++bits;
+        bool in_b = false;
+        if (S->nnz > 0) {
+            PLAN_TRY(radix_sort(tmp.ka, tmp.va, tmp.kb, tmp.vb, S->nnz, bits, tmp.ghist, st, &in_b),
+                     "transpose sort");
+            PLAN_TRY(cudaMemcpyAsync(p->perm_t, in_b ? tmp.vb : tmp.va,
+                                     sizeof(int32_t) * (size_t)S->nnz, cudaMemcpyDeviceToDevice, st),
+                     "copy perm");
+            rows_of_kernel<<<blocks_for(S->nnz, 256, 152 * 32), 256, 0, st>>>(
+                S->row_ptr, S->m, p->perm_t, p->col_idx_t, S->nnz);
+            PLAN_TRY(cudaGetLastError(), "transpose rows");
+        }
+        rc = build_side(p->cols, p->row_ptr_t, S->n, p->split_nnz, r, tmp, st, p);
+        if (rc) return fail(rc);
+        p->cols.col_idx = p->col_idx_t;
+        p->cols.perm = p->perm_t;
+    } else {
+        p->cols.max_nnz = -1;
+    }
+    PLAN_TRY(cudaStreamSynchronize(st), "plan sync");
+#undef PLAN_TRY
+    *out = p;
+    return FMM_OK;
+}
+
+__global__ void combine_kernel(const int4 *split, int32_t n_split, const float *partials,
+                               float *out, int32_t r)
+{
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= n_split)
+        return;
+    const int4 sp = split[w];
+    for (int k = lane; k < r; k += 32) {
+        float acc = 0.f;
+        for (int c = 0; c < sp.z; ++c)
+            acc += partials[(size_t)(sp.y + c) * r + k];
+        out[(size_t)sp.x * r + k] = acc;
+    }
+}
+
+cudaError_t launch_combine(const Side &side, float *out, int32_t r, cudaStream_t st)
+{
+    if (side.n_split == 0 || !out)
+        return cudaSuccess;
+    combine_kernel<<<(side.n_split + 7) / 8, 256, 0, st>>>(side.split, side.n_split,
+                                                           side.partials, out, r);
+    return cudaGetLastError();
+}
+
+}  // namespace fmm

@@ -1,0 +1,434 @@
+// Row-pass kernels of libfmm.
+//
+// Every operation of the library is one "row pass" over a CSR (S, or S^T with
+// a permutation back to the CSR slots of S): a group of G lanes owns one
+// output row (or one chunk of a split row), keeps that row's local operands
+// in registers, and walks the row's nonzeros U at a time.  For each nonzero
+// it gathers one dense row through col_idx with 16-byte loads, forms the
+// sampled inner products with per-lane partial sums and an xor-shuffle
+// reduction inside the group, and folds the result into a register
+// accumulator.  The output row is written once.  This is the local kernel
+// fusion of Sec. IV-B (2): in the fused roles the SDDMM value of a nonzero
+// (Sec. II, Eq. 1) lives in a register for the few instructions between the
+// reduction and the accumulation, and never reaches memory.
+//
+// Roles (Mode):
+//   M_FUSED    acc += s * <L_i, Y_j> * Y_j          FusedMMA / FusedMMB
+//   M_SDDMM    v[p] = s * <L_i, Y_j>                SDDMM (Eq. 1)
+//   M_SPMM     acc += v[p] * Y_j                    SpMMA / SpMMB
+//   M_BWD_ROW  ds[p] = <L_i,Y_j> <H_i,Y_j>;  acc += s <H_i,Y_j> Y_j
+//   M_BWD_COL  acc += s (<Y_i,L_j> H_i + <H_i,L_j> Y_i)   (H_i gathered too)
+#pragma once
+
+#include "fmm_internal.cuh"
+
+namespace fmm {
+
+typedef uint16_t bf16_t;   // bfloat16 bits
+
+template <typename T> struct Elem;
+template <> struct Elem<float> { static constexpr int PER16 = 4; };
+template <> struct Elem<bf16_t> { static constexpr int PER16 = 8; };
+
+// Lane layout of one dense row of r elements of type T: the row is split
+// into 16-byte vectors; a group of G lanes (G = min(32, vectors)) owns it,
+// lane l holding vectors l, l + G, ...  Element k of lane l, vector v,
+// position t is k = (v * G + l) * EPV + t.
+template <typename T, int R>
+struct Shape {
+    static constexpr int ROW_BYTES = R * (int)sizeof(T);
+    static constexpr int VECS = ROW_BYTES / 16;
+    static constexpr int G = VECS < 32 ? VECS : 32;
+    static constexpr int VPL = VECS / G;
+    static constexpr int EPV = Elem<T>::PER16;
+    static constexpr int E = VPL * EPV;
+    static_assert(ROW_BYTES % 16 == 0 && VECS % G == 0, "unsupported r");
+};
+
+__device__ __forceinline__ void unpack_bf16x8(const uint4 q, float *f)
+{
+    f[0] = __uint_as_float(q.x << 16); f[1] = __uint_as_float(q.x & 0xffff0000u);
+    f[2] = __uint_as_float(q.y << 16); f[3] = __uint_as_float(q.y & 0xffff0000u);
+    f[4] = __uint_as_float(q.z << 16); f[5] = __uint_as_float(q.z & 0xffff0000u);
+    f[6] = __uint_as_float(q.w << 16); f[7] = __uint_as_float(q.w & 0xffff0000u);
+}
+
+// Loads one dense row of T into the lane's registers (widened to float).
+// STREAM: read-once data (evict-first); otherwise the read-only path.
+template <typename T, int R, bool STREAM>
+__device__ __forceinline__ void load_row(const T *row, int lig, float (&f)[Shape<T, R>::E])
+{
+    using S = Shape<T, R>;
+#pragma unroll
+    for (int v = 0; v < S::VPL; ++v) {
+        const int vec = v * S::G + lig;
+        if constexpr (sizeof(T) == 4) {
+            const float4 *p = reinterpret_cast<const float4 *>(row) + vec;
+            const float4 q = STREAM ? __ldcs(p) : __ldg(p);
+            f[v * 4 + 0] = q.x; f[v * 4 + 1] = q.y; f[v * 4 + 2] = q.z; f[v * 4 + 3] = q.w;
+        } else {
+            const uint4 *p = reinterpret_cast<const uint4 *>(row) + vec;
+            const uint4 q = STREAM ? __ldcs(p) : __ldg(p);
+            unpack_bf16x8(q, &f[v * 8]);
+        }
+    }
+}
+
+// A float32 row laid out with T's element mapping (gradient rows).
+template <typename T, int R, bool STREAM>
+__device__ __forceinline__ void load_row_f32(const float *row, int lig, float (&f)[Shape<T, R>::E])
+{
+    using S = Shape<T, R>;
+#pragma unroll
+    for (int v = 0; v < S::VPL; ++v) {
+#pragma unroll
+        for (int q = 0; q < S::EPV / 4; ++q) {
+            const int k = (v * S::G + lig) * S::EPV + 4 * q;
+            const float4 *p = reinterpret_cast<const float4 *>(row + k);
+            const float4 x = STREAM ? __ldcs(p) : __ldg(p);
+            f[v * S::EPV + 4 * q + 0] = x.x; f[v * S::EPV + 4 * q + 1] = x.y;
+            f[v * S::EPV + 4 * q + 2] = x.z; f[v * S::EPV + 4 * q + 3] = x.w;
+        }
+    }
+}
+
+template <typename T, int R>
+__device__ __forceinline__ void store_row_f32(float *row, int lig, const float (&f)[Shape<T, R>::E])
+{
+    using S = Shape<T, R>;
+#pragma unroll
+    for (int v = 0; v < S::VPL; ++v) {
+#pragma unroll
+        for (int q = 0; q < S::EPV / 4; ++q) {
+            const int k = (v * S::G + lig) * S::EPV + 4 * q;
+            const int e = v * S::EPV + 4 * q;
+            __stcs(reinterpret_cast<float4 *>(row + k),
+                   make_float4(f[e + 0], f[e + 1], f[e + 2], f[e + 3]));
+        }
+    }
+}
+
+// Sum over the G lanes of a group (xor butterfly; every lane gets the sum).
+template <int G, int NV>
+__device__ __forceinline__ void group_allreduce(float (&v)[NV])
+{
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i)
+            v[i] += __shfl_xor_sync(0xffffffffu, v[i], off);
+    }
+}
+
+// Work item of group `gid`: chunks of split rows first, then light rows in
+// plan order.  slot >= 0 marks a chunk (its partial row goes to partials).
+__device__ __forceinline__ void pass_item(const PassArgs &a, long long gid, int &row,
+                                          int &beg, int &end, int &slot)
+{
+    if (gid < a.n_chunks) {
+        const int4 c = a.chunks[gid];
+        row = c.x; beg = c.y; end = c.z; slot = (int)gid;
+    } else {
+        row = a.order[gid - a.n_chunks];
+        beg = __ldg(a.row_ptr + row);
+        end = __ldg(a.row_ptr + row + 1);
+        slot = -1;
+    }
+}
+
+template <int MODE, typename T, int R, int U>
+__global__ void __launch_bounds__(256) row_pass_kernel(const PassArgs a)
+{
+    using S = Shape<T, R>;
+    constexpr int G = S::G, E = S::E;
+    constexpr bool HAS_L = MODE != M_SPMM;
+    constexpr bool ACC = MODE != M_SDDMM;
+    constexpr bool TWO = MODE == M_BWD_ROW || MODE == M_BWD_COL;
+    constexpr int ND = TWO ? 2 * U : U;
+
+    const int lane = threadIdx.x & 31;
+    const int lig = lane & (G - 1);
+    const long long gid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const long long total = (long long)a.n_chunks + a.n_light;
+    const bool active = gid < total;
+
+    int row = 0, beg = 0, end = 0, slot = -1;
+    if (active)
+        pass_item(a, gid, row, beg, end, slot);
+
+    const T *L = static_cast<const T *>(a.L);
+    const T *Y = static_cast<const T *>(a.Y);
+
+    float lrow[E], hrow[E], acc[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) { lrow[e] = 0.f; hrow[e] = 0.f; acc[e] = 0.f; }
+    if (HAS_L && active)
+        load_row<T, R, true>(L + (size_t)row * R, lig, lrow);
+    if (MODE == M_BWD_ROW && active)
+        load_row_f32<T, R, true>(a.H + (size_t)row * R, lig, hrow);
+
+    const int iters = (end - beg + U - 1) / U;
+    const int witers = (int)__reduce_max_sync(0xffffffffu, (unsigned)iters);
+
+    for (int it = 0; it < witers; ++it) {
+        const int p0 = beg + it * U;
+        int jj[U], sidx[U];
+        float sv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int p = p0 + u;
+            if (p < end) {
+                jj[u] = __ldg(a.col_idx + p);
+                sidx[u] = a.perm ? __ldg(a.perm + p) : p;
+                sv[u] = a.s ? __ldg(a.s + sidx[u]) : 1.f;
+            } else {
+                jj[u] = -1; sidx[u] = 0; sv[u] = 0.f;
+            }
+        }
+        float y[U][E];
+        float h[MODE == M_BWD_COL ? U : 1][E];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (jj[u] >= 0) {
+                load_row<T, R, false>(Y + (size_t)jj[u] * R, lig, y[u]);
+                if constexpr (MODE == M_BWD_COL)
+                    load_row_f32<T, R, false>(a.H + (size_t)jj[u] * R, lig, h[u]);
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    y[u][e] = 0.f;
+                    if constexpr (MODE == M_BWD_COL) h[u][e] = 0.f;
+                }
+            }
+        }
+        if constexpr (MODE == M_SPMM) {
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (jj[u] >= 0) {
+#pragma unroll
+                    for (int e = 0; e < E; ++e)
+                        acc[e] = fmaf(sv[u], y[u][e], acc[e]);
+                }
+        } else {
+            float d[ND];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                float t = 0.f;
+#pragma unroll
+                for (int e = 0; e < E; ++e)
+                    t = fmaf(lrow[e], y[u][e], t);
+                d[u] = t;
+                if constexpr (MODE == M_BWD_ROW) {
+                    float w = 0.f;
+#pragma unroll
+                    for (int e = 0; e < E; ++e)
+                        w = fmaf(hrow[e], y[u][e], w);
+                    d[U + u] = w;
+                } else if constexpr (MODE == M_BWD_COL) {
+                    float w = 0.f;
+#pragma unroll
+                    for (int e = 0; e < E; ++e)
+                        w = fmaf(h[u][e], lrow[e], w);
+                    d[U + u] = w;
+                }
+            }
+            group_allreduce<G, ND>(d);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (jj[u] < 0)
+                    continue;
+                if constexpr (MODE == M_FUSED) {
+                    const float c = sv[u] * d[u];
+#pragma unroll
+                    for (int e = 0; e < E; ++e)
+                        acc[e] = fmaf(c, y[u][e], acc[e]);
+                } else if constexpr (MODE == M_SDDMM) {
+                    if (lig == (u % G))
+                        a.nzout[sidx[u]] = sv[u] * d[u];
+                } else if constexpr (MODE == M_BWD_ROW) {
+                    if (a.nzout && lig == (u % G))
+                        a.nzout[sidx[u]] = d[u] * d[U + u];
+                    const float c = sv[u] * d[U + u];
+#pragma unroll
+                    for (int e = 0; e < E; ++e)
+                        acc[e] = fmaf(c, y[u][e], acc[e]);
+                } else {  // M_BWD_COL
+                    const float c1 = sv[u] * d[u], c2 = sv[u] * d[U + u];
+#pragma unroll
+                    for (int e = 0; e < E; ++e)
+                        acc[e] = fmaf(c1, h[u][e], fmaf(c2, y[u][e], acc[e]));
+                }
+            }
+        }
+    }
+
+    if (ACC && active) {
+        float *dst = slot >= 0 ? a.partials + (size_t)slot * R
+                               : (a.out ? a.out + (size_t)row * R : nullptr);
+        if (dst)
+            store_row_f32<T, R>(dst, lig, acc);
+    }
+}
+
+template <typename T> __device__ __forceinline__ float widen(T x);
+template <> __device__ __forceinline__ float widen<float>(float x) { return x; }
+template <> __device__ __forceinline__ float widen<bf16_t>(bf16_t x)
+{
+    return __uint_as_float(((uint32_t)x) << 16);
+}
+
+__device__ __forceinline__ float warp_allreduce(float v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+        v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// Generic pass for any r and any alignment: one warp per row or chunk,
+// scalar loads strided by lane, the output row accumulated in place (each
+// lane owns the columns k = lane + 32 t, so no two lanes touch one word).
+template <int MODE, typename T>
+__global__ void __launch_bounds__(256) row_pass_generic(const PassArgs a)
+{
+    constexpr bool ACC = MODE != M_SDDMM;
+    const int lane = threadIdx.x & 31;
+    const long long gid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long total = (long long)a.n_chunks + a.n_light;
+    if (gid >= total)
+        return;   // uniform per warp
+    int row, beg, end, slot;
+    pass_item(a, gid, row, beg, end, slot);
+    const int r = a.r;
+    const T *L = static_cast<const T *>(a.L);
+    const T *Y = static_cast<const T *>(a.Y);
+    float *dst = nullptr;
+    if (ACC)
+        dst = slot >= 0 ? a.partials + (size_t)slot * r
+                        : (a.out ? a.out + (size_t)row * r : nullptr);
+    if (dst)
+        for (int k = lane; k < r; k += 32)
+            dst[k] = 0.f;
+    const T *Li = L ? L + (size_t)row * r : nullptr;
+    for (int p = beg; p < end; ++p) {
+        const int j = __ldg(a.col_idx + p);
+        const int sidx = a.perm ? __ldg(a.perm + p) : p;
+        const float sv = a.s ? __ldg(a.s + sidx) : 1.f;
+        const T *Yj = Y + (size_t)j * r;
+        float d = 0.f, w = 0.f;
+        if constexpr (MODE != M_SPMM) {
+            for (int k = lane; k < r; k += 32) {
+                const float yk = widen<T>(Yj[k]);
+                d = fmaf(widen<T>(Li[k]), yk, d);
+                if constexpr (MODE == M_BWD_ROW)
+                    w = fmaf(a.H[(size_t)row * r + k], yk, w);
+                if constexpr (MODE == M_BWD_COL)
+                    w = fmaf(a.H[(size_t)j * r + k], widen<T>(Li[k]), w);
+            }
+            d = warp_allreduce(d);
+            if constexpr (MODE == M_BWD_ROW || MODE == M_BWD_COL)
+                w = warp_allreduce(w);
+        }
+        if constexpr (MODE == M_SDDMM) {
+            if (lane == 0)
+                a.nzout[sidx] = sv * d;
+        } else if constexpr (MODE == M_BWD_ROW) {
+            if (lane == 0 && a.nzout)
+                a.nzout[sidx] = d * w;
+        }
+        if (dst) {
+            if constexpr (MODE == M_FUSED) {
+                const float c = sv * d;
+                for (int k = lane; k < r; k += 32)
+                    dst[k] = fmaf(c, widen<T>(Yj[k]), dst[k]);
+            } else if constexpr (MODE == M_SPMM) {
+                for (int k = lane; k < r; k += 32)
+                    dst[k] = fmaf(sv, widen<T>(Yj[k]), dst[k]);
+            } else if constexpr (MODE == M_BWD_ROW) {
+                const float c = sv * w;
+                for (int k = lane; k < r; k += 32)
+                    dst[k] = fmaf(c, widen<T>(Yj[k]), dst[k]);
+            } else if constexpr (MODE == M_BWD_COL) {
+                const float c1 = sv * d, c2 = sv * w;
+                for (int k = lane; k < r; k += 32)
+                    dst[k] = fmaf(c1, a.H[(size_t)j * r + k],
+                                  fmaf(c2, widen<T>(Yj[k]), dst[k]));
+            }
+        }
+    }
+}
+
+constexpr int unroll_cap(int mode, int E)
+{
+    return (mode == M_BWD_COL ? 32 : 64) / E;
+}
+
+template <int MODE, typename T, int R, int U>
+cudaError_t launch_vec(const PassArgs &a, cudaStream_t st)
+{
+    constexpr int G = Shape<T, R>::G;
+    const long long total = (long long)a.n_chunks + a.n_light;
+    const long long threads = total * G;
+    const long long blocks = (threads + 255) / 256;
+    row_pass_kernel<MODE, T, R, U><<<(unsigned)blocks, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int MODE, typename T, int R>
+cudaError_t dispatch_unroll(int unroll, const PassArgs &a, cudaStream_t st)
+{
+    constexpr int CAP = unroll_cap(MODE, Shape<T, R>::E);
+    if (unroll >= 8 && CAP >= 8)
+        return launch_vec<MODE, T, R, 8>(a, st);
+    return launch_vec<MODE, T, R, 4>(a, st);
+}
+
+template <typename T, int R>
+cudaError_t dispatch_mode(int mode, int unroll, const PassArgs &a, cudaStream_t st)
+{
+    switch (mode) {
+    case M_FUSED: return dispatch_unroll<M_FUSED, T, R>(unroll, a, st);
+    case M_SDDMM: return dispatch_unroll<M_SDDMM, T, R>(unroll, a, st);
+    case M_SPMM: return dispatch_unroll<M_SPMM, T, R>(unroll, a, st);
+    case M_BWD_ROW: return dispatch_unroll<M_BWD_ROW, T, R>(unroll, a, st);
+    case M_BWD_COL: return dispatch_unroll<M_BWD_COL, T, R>(unroll, a, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t launch_generic(int mode, const PassArgs &a, cudaStream_t st)
+{
+    const long long total = (long long)a.n_chunks + a.n_light;
+    const long long blocks = (total + 7) / 8;
+    switch (mode) {
+    case M_FUSED: row_pass_generic<M_FUSED, T><<<(unsigned)blocks, 256, 0, st>>>(a); break;
+    case M_SDDMM: row_pass_generic<M_SDDMM, T><<<(unsigned)blocks, 256, 0, st>>>(a); break;
+    case M_SPMM: row_pass_generic<M_SPMM, T><<<(unsigned)blocks, 256, 0, st>>>(a); break;
+    case M_BWD_ROW: row_pass_generic<M_BWD_ROW, T><<<(unsigned)blocks, 256, 0, st>>>(a); break;
+    case M_BWD_COL: row_pass_generic<M_BWD_COL, T><<<(unsigned)blocks, 256, 0, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_pass_typed(int mode, int unroll, bool vec, const PassArgs &a,
+                              cudaStream_t st)
+{
+    const long long total = (long long)a.n_chunks + a.n_light;
+    if (total == 0)
+        return cudaSuccess;
+    if (vec) {
+        switch (a.r) {
+        case 32: return dispatch_mode<T, 32>(mode, unroll, a, st);
+        case 64: return dispatch_mode<T, 64>(mode, unroll, a, st);
+        case 128: return dispatch_mode<T, 128>(mode, unroll, a, st);
+        case 256: return dispatch_mode<T, 256>(mode, unroll, a, st);
+        default: break;
+        }
+    }
+    return launch_generic<T>(mode, a, st);
+}
+
+}  // namespace fmm

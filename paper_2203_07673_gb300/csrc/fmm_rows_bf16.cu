@@ -1,0 +1,9 @@
+// bfloat16-input instantiations of the row-pass kernels (float32 accumulation).
+#include "fmm_rows.cuh"
+
+namespace fmm {
+cudaError_t launch_pass_bf16(int mode, int unroll, bool vec, const PassArgs &a, cudaStream_t st)
+{
+    return launch_pass_typed<bf16_t>(mode, unroll, vec, a, st);
+}
+}  // namespace fmm

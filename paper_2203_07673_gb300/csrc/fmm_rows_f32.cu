@@ -1,0 +1,9 @@
+// float32 instantiations of the row-pass kernels.
+#include "fmm_rows.cuh"
+
+namespace fmm {
+cudaError_t launch_pass_f32(int mode, int unroll, bool vec, const PassArgs &a, cudaStream_t st)
+{
+    return launch_pass_typed<float>(mode, unroll, vec, a, st);
+}
+}  // namespace fmm

@@ -1,0 +1,281 @@
+"""Thin Python binding of libfmm (the C ABI in include/fmm.h).
+
+Argument marshalling only: every function checks tensor devices, dtypes and
+shapes, passes raw device pointers and the current CUDA stream to the C entry
+point of the same name, and raises ``FmmError`` on a nonzero status.  All
+computation happens in the library's CUDA kernels; there is no CPU path.  If
+the library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libfmm.so")
+
+FMM_OK, FMM_EINVAL, FMM_EUNSUPPORTED, FMM_EOVERFLOW, FMM_ECUDA, FMM_ENOMEM = 0, -1, -2, -3, -4, -5
+FMM_F32, FMM_BF16 = 0, 1
+FMM_PLAN_NO_TRANSPOSE = 1
+
+# Every function of the C ABI, with its ctypes argument types.
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_SIGNATURES = {
+    "fmm_csr_validate": ([_P, _P, _P], ctypes.c_int),
+    "fmm_plan_create": ([_P, _I32, _I32, _P, _P, _P], ctypes.c_int),
+    "fmm_plan_destroy": ([_P], ctypes.c_int),
+    "fmm_plan_get_info": ([_P, _P], ctypes.c_int),
+    "fmm_sddmm": ([_P, _P, _P, _P, _P, _P], ctypes.c_int),
+    "fmm_spmm": ([_P, _P, _P, _P, _P], ctypes.c_int),
+    "fmm_spmm_t": ([_P, _P, _P, _P, _P], ctypes.c_int),
+    "fmm_fusedmm": ([_P, _P, _P, _P, _P, _P], ctypes.c_int),
+    "fmm_fusedmm_t": ([_P, _P, _P, _P, _P, _P], ctypes.c_int),
+    "fmm_fusedmm_bwd": ([_P, _P, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
+    "fmm_fusedmm_t_bwd": ([_P, _P, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
+    "fmm_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    "fmm_last_error": ([], ctypes.c_char_p),
+    "fmm_version": ([], ctypes.c_int32),
+}
+
+
+class FmmError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{where}: status {status} ({status_string(status)}) {detail}".rstrip())
+
+
+class _Csr(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int32), ("n", ctypes.c_int32), ("nnz", ctypes.c_int64),
+                ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p)]
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("flags", ctypes.c_uint32), ("split_nnz", ctypes.c_int32),
+                ("unroll", ctypes.c_int32)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int32), ("n", ctypes.c_int32), ("r", ctypes.c_int32),
+                ("dtype", ctypes.c_int32), ("nnz", ctypes.c_int64),
+                ("max_row_nnz", ctypes.c_int32), ("max_col_nnz", ctypes.c_int32),
+                ("split_rows", ctypes.c_int32), ("split_cols", ctypes.c_int32),
+                ("row_chunks", ctypes.c_int32), ("col_chunks", ctypes.c_int32),
+                ("split_nnz", ctypes.c_int32), ("unroll", ctypes.c_int32),
+                ("workspace_bytes", ctypes.c_int64)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libfmm (raises if it is not built or cannot be loaded)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libfmm is not built ({LIB_PATH} missing); "
+                                   "run __graft_entry__.build() or "
+                                   "python -m paper_2203_07673_gb300.build")
+            handle = ctypes.CDLL(LIB_PATH)
+            for name, (args, res) in _SIGNATURES.items():
+                fn = getattr(handle, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = handle
+    return _lib
+
+
+def status_string(status: int) -> str:
+    try:
+        return lib().fmm_status_string(int(status)).decode()
+    except Exception:  # the library itself is missing
+        return "?"
+
+
+def last_error() -> str:
+    return lib().fmm_last_error().decode()
+
+
+def _check(rc: int, where: str):
+    if rc != FMM_OK:
+        raise FmmError(rc, where, last_error())
+
+
+def _stream(stream=None) -> int:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return s.cuda_stream
+
+
+_DT = {torch.float32: FMM_F32, torch.bfloat16: FMM_BF16}
+
+
+def _ptr(t, name, dtype=None, shape=None, device=None):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be on a CUDA device")
+    if device is not None and t.device != device:
+        raise ValueError(f"{name} is on {t.device}, the plan on {device}")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr() if t.numel() else None
+
+
+class Plan:
+    """A preprocessed sparse pattern (the C ``fmm_plan``).
+
+    ``row_ptr`` (m + 1) and ``col_idx`` (nnz) are int32 CUDA tensors; the plan
+    keeps references to them, and they must not be modified while it lives.
+    ``dtype`` is the dense operand dtype (torch.float32 or torch.bfloat16).
+    """
+
+    def __init__(self, row_ptr: torch.Tensor, col_idx: torch.Tensor, n: int, r: int,
+                 dtype=torch.float32, transpose: bool = True, split_nnz: int = 0,
+                 unroll: int = 0, stream=None):
+        if dtype not in _DT:
+            raise TypeError(f"unsupported dtype {dtype}")
+        self.handle = None
+        self.device = row_ptr.device
+        _ptr(row_ptr, "row_ptr", torch.int32)
+        _ptr(col_idx, "col_idx", torch.int32, device=self.device)
+        if row_ptr.dim() != 1 or col_idx.dim() != 1 or row_ptr.numel() < 1:
+            raise ValueError("row_ptr and col_idx must be 1-D (row_ptr with m + 1 entries)")
+        self.row_ptr, self.col_idx = row_ptr, col_idx
+        self.m, self.n, self.r = row_ptr.numel() - 1, int(n), int(r)
+        self.nnz = col_idx.numel()
+        self.dtype = dtype
+        csr = _Csr(self.m, self.n, self.nnz, row_ptr.data_ptr(),
+                   col_idx.data_ptr() if self.nnz else None)
+        opt = _Options(0 if transpose else FMM_PLAN_NO_TRANSPOSE, int(split_nnz), int(unroll))
+        out = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            rc = lib().fmm_plan_create(ctypes.byref(csr), self.r, _DT[dtype], ctypes.byref(opt),
+                                       _stream(stream), ctypes.byref(out))
+        _check(rc, "fmm_plan_create")
+        self.handle = out.value
+
+    def info(self) -> dict:
+        inf = _Info()
+        _check(lib().fmm_plan_get_info(self.handle, ctypes.byref(inf)), "fmm_plan_get_info")
+        return {name: getattr(inf, name) for name, _ in _Info._fields_}
+
+    def close(self):
+        if self.handle is not None:
+            lib().fmm_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # shape helpers
+    def _dense(self, t, rows, name):
+        return _ptr(t, name, self.dtype, (rows, self.r), self.device)
+
+    def _f32(self, t, shape, name):
+        return _ptr(t, name, torch.float32, shape, self.device)
+
+
+def validate(row_ptr: torch.Tensor, col_idx: torch.Tensor, n: int, stream=None) -> int:
+    """fmm_csr_validate: -1 if valid, else the first bad index (see fmm.h)."""
+    csr = _Csr(row_ptr.numel() - 1, int(n), col_idx.numel(), row_ptr.data_ptr(),
+               col_idx.data_ptr() if col_idx.numel() else None)
+    bad = ctypes.c_int64(-1)
+    rc = lib().fmm_csr_validate(ctypes.byref(csr), _stream(stream), ctypes.byref(bad))
+    if rc not in (FMM_OK, FMM_EINVAL):
+        _check(rc, "fmm_csr_validate")
+    return int(bad.value)
+
+
+def _out(out, shape, plan):
+    if out is None:
+        return torch.empty(shape, dtype=torch.float32, device=plan.device)
+    return out
+
+
+def sddmm(plan: Plan, vals, A, B, out=None, stream=None):
+    out = _out(out, (plan.nnz,), plan)
+    rc = lib().fmm_sddmm(plan.handle, plan._f32(vals, (plan.nnz,), "vals"),
+                         plan._dense(A, plan.m, "A"), plan._dense(B, plan.n, "B"),
+                         plan._f32(out, (plan.nnz,), "out"), _stream(stream))
+    _check(rc, "fmm_sddmm")
+    return out
+
+
+def spmm(plan: Plan, v, B, out=None, stream=None):
+    out = _out(out, (plan.m, plan.r), plan)
+    rc = lib().fmm_spmm(plan.handle, plan._f32(v, (plan.nnz,), "v"),
+                        plan._dense(B, plan.n, "B"), plan._f32(out, (plan.m, plan.r), "out"),
+                        _stream(stream))
+    _check(rc, "fmm_spmm")
+    return out
+
+
+def spmm_t(plan: Plan, v, A, out=None, stream=None):
+    out = _out(out, (plan.n, plan.r), plan)
+    rc = lib().fmm_spmm_t(plan.handle, plan._f32(v, (plan.nnz,), "v"),
+                          plan._dense(A, plan.m, "A"), plan._f32(out, (plan.n, plan.r), "out"),
+                          _stream(stream))
+    _check(rc, "fmm_spmm_t")
+    return out
+
+
+def fusedmm(plan: Plan, vals, A, B, out=None, stream=None):
+    out = _out(out, (plan.m, plan.r), plan)
+    rc = lib().fmm_fusedmm(plan.handle, plan._f32(vals, (plan.nnz,), "vals"),
+                           plan._dense(A, plan.m, "A"), plan._dense(B, plan.n, "B"),
+                           plan._f32(out, (plan.m, plan.r), "out"), _stream(stream))
+    _check(rc, "fmm_fusedmm")
+    return out
+
+
+def fusedmm_t(plan: Plan, vals, A, B, out=None, stream=None):
+    out = _out(out, (plan.n, plan.r), plan)
+    rc = lib().fmm_fusedmm_t(plan.handle, plan._f32(vals, (plan.nnz,), "vals"),
+                             plan._dense(A, plan.m, "A"), plan._dense(B, plan.n, "B"),
+                             plan._f32(out, (plan.n, plan.r), "out"), _stream(stream))
+    _check(rc, "fmm_fusedmm_t")
+    return out
+
+
+def fusedmm_bwd(plan: Plan, vals, A, B, G, need=(True, True, True), stream=None):
+    """Returns (dA, dB, ds) (float32; None where need is False)."""
+    dA = torch.empty((plan.m, plan.r), dtype=torch.float32, device=plan.device) if need[0] else None
+    dB = torch.empty((plan.n, plan.r), dtype=torch.float32, device=plan.device) if need[1] else None
+    ds = torch.empty((plan.nnz,), dtype=torch.float32, device=plan.device) if need[2] else None
+    rc = lib().fmm_fusedmm_bwd(plan.handle, plan._f32(vals, (plan.nnz,), "vals"),
+                               plan._dense(A, plan.m, "A"), plan._dense(B, plan.n, "B"),
+                               plan._f32(G, (plan.m, plan.r), "G"),
+                               plan._f32(dA, (plan.m, plan.r), "dA"),
+                               plan._f32(dB, (plan.n, plan.r), "dB"),
+                               plan._f32(ds, (plan.nnz,), "ds"), _stream(stream))
+    _check(rc, "fmm_fusedmm_bwd")
+    return dA, dB, ds
+
+
+def fusedmm_t_bwd(plan: Plan, vals, A, B, Gn, need=(True, True, True), stream=None):
+    """Returns (dA, dB, ds) for L = <Gn, FusedMMB>."""
+    dA = torch.empty((plan.m, plan.r), dtype=torch.float32, device=plan.device) if need[0] else None
+    dB = torch.empty((plan.n, plan.r), dtype=torch.float32, device=plan.device) if need[1] else None
+    ds = torch.empty((plan.nnz,), dtype=torch.float32, device=plan.device) if need[2] else None
+    rc = lib().fmm_fusedmm_t_bwd(plan.handle, plan._f32(vals, (plan.nnz,), "vals"),
+                                 plan._dense(A, plan.m, "A"), plan._dense(B, plan.n, "B"),
+                                 plan._f32(Gn, (plan.n, plan.r), "Gn"),
+                                 plan._f32(dA, (plan.m, plan.r), "dA"),
+                                 plan._f32(dB, (plan.n, plan.r), "dB"),
+                                 plan._f32(ds, (plan.nnz,), "ds"), _stream(stream))
+    _check(rc, "fmm_fusedmm_t_bwd")
+    return dA, dB, ds
