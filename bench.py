@@ -146,16 +146,16 @@ def oracle_sample(w, seconds: float, rows_hint: int | None = None):
         t0 = time.perf_counter()
         oracle.fusedmm(rp, ci, v, a, b, n)
         oracle.fusedmm_t(rp, ci, v, a, b, n)
-        return time.perf_counter() - t0, nnz
+        return time.perf_counter() - t0, nnz, n
 
     rows = rows_hint or min(S.m, 1024)
-    t, nnz = run(rows)
+    t, nnz, ncols = run(rows)
     if rows_hint is None:
         rows = int(min(S.m, max(rows, rows * seconds / max(t, 1e-6))))
-        t, nnz = run(rows)
+        t, nnz, ncols = run(rows)
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     desc = (f"first {rows} of {S.m} rows ({nnz} nnz, {nnz / max(S.nnz, 1):.2%} of the "
-            f"workload), columns remapped to the {min(S.n, nnz)}-or-fewer they touch; "
+            f"workload), columns remapped to the {ncols} they touch; "
             f"FusedMMA + FusedMMB in FP64 (oracle/fmm_oracle.c); FusedMMA rows on "
             f"{threads} OpenMP threads, the FusedMMB scatter on 1")
     return 2.0 * nnz * r / t, desc, threads, rows
