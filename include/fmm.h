@@ -204,6 +204,30 @@ int fmm_fusedmm_t_bwd(const fmm_plan *plan, const float *vals, const void *A,
                       const void *B, const float *Gn, float *dA, float *dB,
                       float *ds, fmm_stream stream);
 
+/*
+ * FusedMMA (same result as fmm_fusedmm) for callers that cannot allocate
+ * device memory: no plan, no cudaMalloc, no allocating library call.  The
+ * paper has no counterpart; this is an interface for memory-constrained
+ * callers (a caller inside a pool or arena that owns all device memory, or a
+ * runtime that forbids allocation on its hot path).
+ *
+ * S (a valid pattern, see fmm_csr_validate; a malformed one gives
+ * unspecified results but no out-of-bounds access), r >= 1, dtype, vals
+ * (NULL = all ones), A (m x r), B (n x r) and out_m (m x r, float32) are as
+ * for fmm_plan_create and fmm_fusedmm.  The only scratch is a fixed
+ * file-scope device array of 34,603,264 bytes per device (held by every
+ * device that loads the library's module until exit): rows longer than
+ * ch = max(512, ceil(2 nnz / min(65536, 8388608 / r))) nonzeros are split
+ * into chunks whose partial rows live there.  r > 65536 returns
+ * FMM_EOVERFLOW.  The array is shared by all calls: calls that overlap on the
+ * GPU race and give wrong results, so order them on one stream.  The first
+ * call on each device looks the array's address up (cudaGetSymbolAddress)
+ * with that device current; make it before any stream capture.
+ * Asynchronous on the stream; deterministic.
+ */
+int fmm_fusedmm_noalloc(const fmm_csr *S, int32_t r, int32_t dtype, const float *vals,
+                        const void *A, const void *B, float *out_m, fmm_stream stream);
+
 /* Static description of a status code (never NULL). */
 const char *fmm_status_string(int status);
 

@@ -36,6 +36,7 @@ _SIGNATURES = {
     "fmm_fusedmm_t": ([_P, _P, _P, _P, _P, _P], ctypes.c_int),
     "fmm_fusedmm_bwd": ([_P, _P, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "fmm_fusedmm_t_bwd": ([_P, _P, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
+    "fmm_fusedmm_noalloc": ([_P, _I32, _I32, _P, _P, _P, _P, _P], ctypes.c_int),
     "fmm_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "fmm_last_error": ([], ctypes.c_char_p),
     "fmm_version": ([], ctypes.c_int32),
@@ -279,3 +280,23 @@ def fusedmm_t_bwd(plan: Plan, vals, A, B, Gn, need=(True, True, True), stream=No
                                  plan._f32(ds, (plan.nnz,), "ds"), _stream(stream))
     _check(rc, "fmm_fusedmm_t_bwd")
     return dA, dB, ds
+
+
+def fusedmm_noalloc(row_ptr, col_idx, n: int, vals, A, B, out=None, stream=None):
+    """fmm_fusedmm_noalloc: FusedMMA from the CSR directly, with no plan and
+    no device allocation inside the library (``out`` is allocated here by
+    torch if not given).  Calls that overlap on the GPU must not be issued:
+    they share one fixed scratch array."""
+    dt = _DT.get(A.dtype)
+    if dt is None:
+        raise TypeError(f"unsupported dtype {A.dtype}")
+    m, r = A.shape
+    if out is None:
+        out = torch.empty((m, r), dtype=torch.float32, device=A.device)
+    csr = _Csr(m, int(n), col_idx.numel(), _ptr(row_ptr, "row_ptr", torch.int32),
+               _ptr(col_idx, "col_idx", torch.int32))
+    rc = lib().fmm_fusedmm_noalloc(ctypes.byref(csr), int(r), dt, _ptr(vals, "vals", torch.float32),
+                                   _ptr(A, "A"), _ptr(B, "B", A.dtype),
+                                   _ptr(out, "out", torch.float32, (m, r)), _stream(stream))
+    _check(rc, "fmm_fusedmm_noalloc")
+    return out
