@@ -335,7 +335,7 @@ def run_fmm(args, rank, world, local_rank):
     except Exception:
         pass
     launches_per_call = 1 + (1 if info["split_rows"] else 0)
-    launches_per_call_t = 1 + (1 if info["split_cols"] else 0)
+    launches_per_call_t = 1 + (1 if info["split_cols"] else 0) + (1 if vals is not None else 0)
     h2d = A_h.numel() * A_h.element_size() + B_h.numel() * B_h.element_size() + (
         0 if vals_h is None else vals_h.numel() * 4)
     d2h = (out_h.numel() + out_t_h.numel()) * 4
@@ -364,7 +364,8 @@ def run_fmm(args, rank, world, local_rank):
         "gpu_launches": K * (launches_per_call + launches_per_call_t),
         "clocks": clk,
         "plan": {k: info[k] for k in ("max_row_nnz", "max_col_nnz", "split_rows",
-                                      "split_cols", "unroll", "workspace_bytes")},
+                                      "split_cols", "variant", "variant_t",
+                                      "workspace_bytes")},
     }
     if rank == 0 and not args.no_cpu_baseline:
         cv, desc, threads, _ = oracle_sample(w, args.cpu_seconds)

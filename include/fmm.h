@@ -97,8 +97,14 @@ typedef struct fmm_plan_options {
                                  nonzeros than this are split into chunks of
                                  this many nonzeros whose partial rows are
                                  summed in a fixed order; 0 = default (512)  */
-    int32_t unroll;           /* nonzeros in flight per row group in the
-                                 vectorised kernels: 0 = default, or 2, 4, 8 */
+    int32_t variant;          /* kernel variant of the vectorised row passes:
+                                 0 = chosen by the plan; else V*100 + N*10 + U
+                                 with V = vectors per lane (as a multiple of
+                                 the minimum for the row width), N = lane
+                                 groups sharing one output row, U = nonzeros
+                                 per group per batch; one of 114, 118, 222,
+                                 224, 441, 442, 214, 124 (a code that does not
+                                 fit the row width falls back to 118)        */
 } fmm_plan_options;
 
 typedef struct fmm_plan fmm_plan;   /* opaque */
@@ -113,7 +119,8 @@ typedef struct fmm_plan_info {
     int32_t row_chunks;       /* chunks over the split rows                */
     int32_t col_chunks;       /* chunks over the split columns             */
     int32_t split_nnz;        /* chunk size in nonzeros                    */
-    int32_t unroll;           /* nonzeros in flight per row group          */
+    int32_t variant;          /* kernel variant code of passes over S      */
+    int32_t variant_t;        /* kernel variant code of passes over S^T    */
     int64_t workspace_bytes;  /* device bytes owned by the plan            */
 } fmm_plan_info;
 

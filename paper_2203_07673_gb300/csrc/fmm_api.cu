@@ -10,13 +10,38 @@ bool fast_r(int32_t r) { return r == 32 || r == 64 || r == 128 || r == 256; }
 
 static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-cudaError_t launch_pass(int mode, int dtype, int unroll, const PassArgs &a, cudaStream_t st)
+// Variant codes: vectors-per-lane multiple * 100 + groups per team * 10 +
+// nonzeros per group per batch (the combinations instantiated in
+// fmm_rows.cuh; a combination that does not fit a row shape falls back to
+// the shape's default).
+static const int kVariantCodes[] = {114, 118, 222, 224, 441, 442, 214, 124};
+
+bool variant_known(int code)
+{
+    for (int c : kVariantCodes)
+        if (c == code) return true;
+    return false;
+}
+
+KernelVariant decode_variant(int code)
+{
+    KernelVariant v;
+    v.vpl_mult = code / 100;
+    v.ng = (code / 10) % 10;
+    v.u = code % 10;
+    return v;
+}
+
+int encode_variant(const KernelVariant &v) { return v.vpl_mult * 100 + v.ng * 10 + v.u; }
+
+cudaError_t launch_pass(int mode, int dtype, const KernelVariant &v, const PassArgs &a,
+                        cudaStream_t st)
 {
     const bool vec = fast_r(a.r) && aligned16(a.L) && aligned16(a.Y) && aligned16(a.H) &&
                      aligned16(a.out) && aligned16(a.partials);
     if (dtype == FMM_BF16)
-        return launch_pass_bf16(mode, unroll, vec, a, st);
-    return launch_pass_f32(mode, unroll, vec, a, st);
+        return launch_pass_bf16(mode, v.vpl_mult, v.ng, v.u, vec, a, st);
+    return launch_pass_f32(mode, v.vpl_mult, v.ng, v.u, vec, a, st);
 }
 
 }  // namespace fmm
@@ -78,13 +103,23 @@ int run_pass(const fmm_plan *p, const Side &side, int mode, const float *s, cons
     a.n_chunks = side.n_chunks;
     a.partials = side.partials;
     a.s = s;
+    a.s_direct = 0;
     a.L = L;
     a.Y = Y;
     a.H = H;
     a.out = out;
     a.nzout = nzout;
     a.r = p->r;
-    cudaError_t e = launch_pass(mode, p->dtype, p->unroll, a, st);
+    cudaError_t e = cudaSuccess;
+    if (side.perm && s) {
+        // values of S gathered once into the order of S^T, so the pass
+        // streams them instead of fetching one scattered word per nonzero
+        e = launch_permute(s, side.perm, p->vals_t, p->nnz, st);
+        a.s = p->vals_t;
+        a.s_direct = 1;
+    }
+    if (e == cudaSuccess)
+        e = launch_pass(mode, p->dtype, side.variant, a, st);
     if (e == cudaSuccess && mode != M_SDDMM)
         e = launch_combine(side, out, p->r, st);
     if (e != cudaSuccess) {
@@ -134,8 +169,7 @@ int fmm_plan_create(const fmm_csr *S, int32_t r, int32_t dtype, const fmm_plan_o
     }
     if (options) {
         if (options->split_nnz < 0 ||
-            (options->unroll != 0 && options->unroll != 2 && options->unroll != 4 &&
-             options->unroll != 8) ||
+            (options->variant != 0 && !variant_known(options->variant)) ||
             (options->flags & ~FMM_PLAN_NO_TRANSPOSE)) {
             set_error_msg("invalid plan options");
             return FMM_EINVAL;
@@ -169,7 +203,8 @@ int fmm_plan_get_info(const fmm_plan *p, fmm_plan_info *info)
     info->row_chunks = p->rows.n_chunks;
     info->col_chunks = p->cols.n_chunks;
     info->split_nnz = p->split_nnz;
-    info->unroll = p->unroll;
+    info->variant = encode_variant(p->rows.variant);
+    info->variant_t = p->has_t ? encode_variant(p->cols.variant) : 0;
     info->workspace_bytes = p->workspace_bytes;
     return FMM_OK;
 }

@@ -8,6 +8,13 @@
 
 namespace fmm {
 
+// Kernel variant of the vectorised row passes: vectors per lane (as a
+// multiple of the row shape's minimum), groups per team, nonzeros per group
+// per batch.
+struct KernelVariant {
+    int vpl_mult = 1, ng = 1, u = 8;
+};
+
 // One side of a plan: the CSR that a row pass walks (S itself, or S^T with a
 // permutation back to the CSR slots of S) plus its schedule.
 struct Side {
@@ -24,6 +31,7 @@ struct Side {
     int4 *split = nullptr;            // {row, first chunk, chunk count, unused}
     float *partials = nullptr;        // n_chunks x r partial rows
     int32_t max_nnz = 0;              // longest row
+    KernelVariant variant;            // kernel variant of passes over this side
     const int32_t *light_order() const { return order ? order + n_split : nullptr; }
 };
 
@@ -48,7 +56,9 @@ struct PassArgs {
     int32_t n_chunks;
     float *partials;
     // operands
-    const float *s;            // per-nonzero scalars in S order (NULL = 1)
+    const float *s;            // per-nonzero scalars (NULL = 1): in S order, or in
+                               // this CSR's order when s_direct is set
+    int32_t s_direct;
     const void *L;             // local rows (dtype of the plan)
     const void *Y;             // gathered rows (dtype of the plan)
     const float *H;            // float32 gradient rows (local or gathered)
@@ -58,18 +68,27 @@ struct PassArgs {
 };
 
 // Launches one row pass (main kernel; the combine kernel for split rows is
-// separate).  dtype: FMM_F32 / FMM_BF16.  unroll: 2, 4 or 8.
-cudaError_t launch_pass(int mode, int dtype, int unroll, const PassArgs &a,
+// separate).  dtype: FMM_F32 / FMM_BF16.
+cudaError_t launch_pass(int mode, int dtype, const KernelVariant &v, const PassArgs &a,
                         cudaStream_t st);
-cudaError_t launch_pass_f32(int mode, int unroll, bool vec, const PassArgs &a,
+cudaError_t launch_pass_f32(int mode, int vpl_mult, int ng, int u, bool vec, const PassArgs &a,
                             cudaStream_t st);
-cudaError_t launch_pass_bf16(int mode, int unroll, bool vec, const PassArgs &a,
+cudaError_t launch_pass_bf16(int mode, int vpl_mult, int ng, int u, bool vec, const PassArgs &a,
                              cudaStream_t st);
+// dst[q] = src[perm[q]] for q < nnz (values of S into the order of S^T).
+cudaError_t launch_permute(const float *src, const int32_t *perm, float *dst, int64_t nnz,
+                           cudaStream_t st);
 // Sums the partial rows of every split row, in chunk order, into out.
 cudaError_t launch_combine(const Side &side, float *out, int32_t r,
                            cudaStream_t st);
 
 bool fast_r(int32_t r);
+bool variant_known(int code);
+KernelVariant decode_variant(int code);
+int encode_variant(const KernelVariant &v);
+// Default kernel variant of a pass over rows of width r (dtype, average
+// nonzeros per row).
+KernelVariant default_variant(int32_t r, int32_t dtype, double avg_nnz);
 
 // Plan construction and error reporting (fmm_plan.cu).
 int check_csr_args(const fmm_csr *S);
@@ -88,13 +107,14 @@ struct fmm_plan {
     int64_t nnz = 0;
     uint32_t flags = 0;
     int32_t split_nnz = 512;
-    int32_t unroll = 0;
+    int32_t variant = 0;              // requested variant code (0 = default)
     bool has_t = false;
     fmm::Side rows;   // S
     fmm::Side cols;   // S^T
     int32_t *row_ptr_t = nullptr;
     int32_t *col_idx_t = nullptr;
     int32_t *perm_t = nullptr;
+    float *vals_t = nullptr;          // per-call values permuted into S^T order
     int64_t workspace_bytes = 0;
     int device = 0;
 };

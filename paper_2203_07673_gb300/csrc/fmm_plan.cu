@@ -457,6 +457,7 @@ void destroy_plan(fmm_plan *p)
     cudaFree(p->row_ptr_t);
     cudaFree(p->col_idx_t);
     cudaFree(p->perm_t);
+    cudaFree(p->vals_t);
     delete p;
 }
 
@@ -467,7 +468,7 @@ int create_plan(const fmm_csr *S, int32_t r, int32_t dtype, const fmm_plan_optio
     p->m = S->m; p->n = S->n; p->nnz = S->nnz; p->r = r; p->dtype = dtype;
     p->flags = opt ? opt->flags : 0u;
     if (opt && opt->split_nnz > 0) p->split_nnz = opt->split_nnz;
-    p->unroll = (opt && opt->unroll > 0) ? opt->unroll : 8;
+    if (opt) p->variant = opt->variant;
     cudaGetDevice(&p->device);
     Temps tmp;
     const int64_t N = std::max<int64_t>({(int64_t)S->m, (int64_t)S->n, S->nnz, 1});
@@ -493,6 +494,8 @@ int create_plan(const fmm_csr *S, int32_t r, int32_t dtype, const fmm_plan_optio
     if (rc) return fail(rc);
     p->rows.col_idx = S->col_idx;
     p->rows.perm = nullptr;
+    p->rows.variant = p->variant ? decode_variant(p->variant)
+                                 : default_variant(r, dtype, S->m ? (double)S->nnz / S->m : 0.0);
 
     if (!(p->flags & FMM_PLAN_NO_TRANSPOSE)) {
         p->has_t = true;
@@ -523,10 +526,13 @@ int create_plan(const fmm_csr *S, int32_t r, int32_t dtype, const fmm_plan_optio
                 S->row_ptr, S->m, p->perm_t, p->col_idx_t, S->nnz);
             PLAN_TRY(cudaGetLastError(), "transpose rows");
         }
+        PLAN_TRY(dmalloc(&p->vals_t, (size_t)S->nnz, p), "allocate S^T values");
         rc = build_side(p->cols, p->row_ptr_t, S->n, p->split_nnz, r, tmp, st, p);
         if (rc) return fail(rc);
         p->cols.col_idx = p->col_idx_t;
         p->cols.perm = p->perm_t;
+        p->cols.variant = p->variant ? decode_variant(p->variant)
+                                     : default_variant(r, dtype, S->n ? (double)S->nnz / S->n : 0.0);
     } else {
         p->cols.max_nnz = -1;
     }
@@ -534,6 +540,38 @@ int create_plan(const fmm_csr *S, int32_t r, int32_t dtype, const fmm_plan_optio
 #undef PLAN_TRY
     *out = p;
     return FMM_OK;
+}
+
+// Measured on GB300 over ER (32 per row), R-MAT and Zipf-row patterns at
+// r = 64 and 128: one group per output row, 8 elements (32 bytes) per lane
+// and 4 nonzeros per batch is the best or within a few percent of it.
+KernelVariant default_variant(int32_t r, int32_t dtype, double avg_nnz)
+{
+    (void)avg_nnz;
+    KernelVariant v;
+    v.ng = 1;
+    v.u = 4;
+    const int vecs = r * (dtype == FMM_BF16 ? 2 : 4) / 16;
+    // float32 rows of at most 32 vectors hold 4 elements per vector: two
+    // vectors per lane make 8 elements
+    v.vpl_mult = (dtype == FMM_F32 && vecs <= 32) ? 2 : 1;
+    return v;
+}
+
+__global__ void permute_kernel(const float *src, const int32_t *perm, float *dst, int64_t nnz)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nnz; q += stride)
+        dst[q] = __ldg(src + __ldcs(perm + q));
+}
+
+cudaError_t launch_permute(const float *src, const int32_t *perm, float *dst, int64_t nnz,
+                           cudaStream_t st)
+{
+    if (nnz == 0 || !src)
+        return cudaSuccess;
+    permute_kernel<<<blocks_for(nnz, 256, 152 * 16), 256, 0, st>>>(src, perm, dst, nnz);
+    return cudaGetLastError();
 }
 
 __global__ void combine_kernel(const int4 *split, int32_t n_split, const float *partials,

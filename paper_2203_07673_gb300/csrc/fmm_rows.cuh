@@ -53,8 +53,8 @@ __device__ __forceinline__ void unpack_bf16x8(const uint4 q, float *f)
     f[6] = __uint_as_float(q.w << 16); f[7] = __uint_as_float(q.w & 0xffff0000u);
 }
 
-// Loads one dense row of T into the lane's registers (widened to float).
-// STREAM: read-once data (evict-first); otherwise the read-only path.
+// Row loads and stores with fixed cache operators: STREAM = read once
+// (ld.global.cs), else the read-only path.
 template <typename T, int R, bool STREAM>
 __device__ __forceinline__ void load_row(const T *row, int lig, float (&f)[Shape<T, R>::E])
 {
@@ -70,24 +70,6 @@ __device__ __forceinline__ void load_row(const T *row, int lig, float (&f)[Shape
             const uint4 *p = reinterpret_cast<const uint4 *>(row) + vec;
             const uint4 q = STREAM ? __ldcs(p) : __ldg(p);
             unpack_bf16x8(q, &f[v * 8]);
-        }
-    }
-}
-
-// A float32 row laid out with T's element mapping (gradient rows).
-template <typename T, int R, bool STREAM>
-__device__ __forceinline__ void load_row_f32(const float *row, int lig, float (&f)[Shape<T, R>::E])
-{
-    using S = Shape<T, R>;
-#pragma unroll
-    for (int v = 0; v < S::VPL; ++v) {
-#pragma unroll
-        for (int q = 0; q < S::EPV / 4; ++q) {
-            const int k = (v * S::G + lig) * S::EPV + 4 * q;
-            const float4 *p = reinterpret_cast<const float4 *>(row + k);
-            const float4 x = STREAM ? __ldcs(p) : __ldg(p);
-            f[v * S::EPV + 4 * q + 0] = x.x; f[v * S::EPV + 4 * q + 1] = x.y;
-            f[v * S::EPV + 4 * q + 2] = x.z; f[v * S::EPV + 4 * q + 3] = x.w;
         }
     }
 }
@@ -136,11 +118,104 @@ __device__ __forceinline__ void pass_item(const PassArgs &a, long long gid, int 
     }
 }
 
-template <int MODE, typename T, int R, int U>
-__global__ void __launch_bounds__(256) row_pass_kernel(const PassArgs a)
+// Cache operators of the row passes: gathered rows and CSR arrays take the
+// read-only path (ld.global.nc); local rows, read once, and outputs, written
+// once, are evict-first (ld/st.global.cs).
+struct Loader {
+    __device__ __forceinline__ int idx(const int32_t *p) const { return __ldg(p); }
+    __device__ __forceinline__ float val(const float *p) const { return __ldg(p); }
+    __device__ __forceinline__ float4 f4(const void *p, bool gather) const
+    {
+        const float4 *q = static_cast<const float4 *>(p);
+        return gather ? __ldg(q) : __ldcs(q);
+    }
+    __device__ __forceinline__ uint4 u4(const void *p, bool gather) const
+    {
+        const uint4 *q = static_cast<const uint4 *>(p);
+        return gather ? __ldg(q) : __ldcs(q);
+    }
+    __device__ __forceinline__ void st4(float *p, float4 v) const
+    {
+        __stcs(reinterpret_cast<float4 *>(p), v);
+    }
+};
+
+// Team layout of one dense row of R elements of type T: VECS 16-byte vectors
+// held by a group of G = VECS / VPL lanes, lane l owning vectors l, l + G, ...
+// (element k = (v * G + l) * EPV + t).  A team of NG groups owns one output
+// row; group g takes nonzeros g, g + NG, ... of that row.
+template <typename T, int R, int VPL, int NG>
+struct TeamShape {
+    static constexpr int VECS = R * (int)sizeof(T) / 16;
+    static constexpr int G = VECS / VPL;
+    static constexpr int TEAM = G * NG;
+    static constexpr int EPV = Elem<T>::PER16;
+    static constexpr int E = VPL * EPV;
+    static_assert(R * (int)sizeof(T) % 16 == 0 && VECS % VPL == 0 && G >= 1, "layout");
+    static_assert(TEAM <= 32 && 32 % TEAM == 0 && (G & (G - 1)) == 0, "team");
+};
+
+template <typename T, int VPL, int G>
+__device__ __forceinline__ void team_load(const Loader &ld, const T *row, int lig, float *f,
+                                          bool gather)
 {
-    using S = Shape<T, R>;
-    constexpr int G = S::G, E = S::E;
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) {
+        const int vec = v * G + lig;
+        if constexpr (sizeof(T) == 4) {
+            const float4 q = ld.f4(reinterpret_cast<const float4 *>(row) + vec, gather);
+            f[v * 4 + 0] = q.x; f[v * 4 + 1] = q.y; f[v * 4 + 2] = q.z; f[v * 4 + 3] = q.w;
+        } else {
+            const uint4 q = ld.u4(reinterpret_cast<const uint4 *>(row) + vec, gather);
+            unpack_bf16x8(q, &f[v * 8]);
+        }
+    }
+}
+
+// A float32 row (gradients, outputs) with the element mapping of T.
+template <typename T, int VPL, int G>
+__device__ __forceinline__ void team_load_f32(const Loader &ld, const float *row, int lig,
+                                              float *f, bool gather)
+{
+    constexpr int EPV = Elem<T>::PER16;
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) {
+#pragma unroll
+        for (int q = 0; q < EPV / 4; ++q) {
+            const float4 x = ld.f4(row + (v * G + lig) * EPV + 4 * q, gather);
+            f[v * EPV + 4 * q + 0] = x.x; f[v * EPV + 4 * q + 1] = x.y;
+            f[v * EPV + 4 * q + 2] = x.z; f[v * EPV + 4 * q + 3] = x.w;
+        }
+    }
+}
+
+template <typename T, int VPL, int G>
+__device__ __forceinline__ void team_store_f32(const Loader &ld, float *row, int lig,
+                                               const float *f)
+{
+    constexpr int EPV = Elem<T>::PER16;
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) {
+#pragma unroll
+        for (int q = 0; q < EPV / 4; ++q) {
+            const int e = v * EPV + 4 * q;
+            ld.st4(row + (v * G + lig) * EPV + 4 * q,
+                   make_float4(f[e + 0], f[e + 1], f[e + 2], f[e + 3]));
+        }
+    }
+}
+
+// One row pass.  A team of NG x G lanes owns one work item (a light row, or
+// a chunk of a split row); per batch each group handles U nonzeros, so a
+// batch covers NG * U consecutive nonzeros (nonzero base + u * NG + g goes to
+// group g).  Gathers of a batch are all issued before any is used.  After the
+// last batch the NG partial accumulators are summed across the team and
+// group 0 stores the row.
+template <int MODE, typename T, int R, int VPL, int NG, int U>
+__global__ void __launch_bounds__(256) team_pass_kernel(const PassArgs a)
+{
+    using TS = TeamShape<T, R, VPL, NG>;
+    constexpr int G = TS::G, TEAM = TS::TEAM, E = TS::E;
     constexpr bool HAS_L = MODE != M_SPMM;
     constexpr bool ACC = MODE != M_SDDMM;
     constexpr bool TWO = MODE == M_BWD_ROW || MODE == M_BWD_COL;
@@ -148,9 +223,11 @@ __global__ void __launch_bounds__(256) row_pass_kernel(const PassArgs a)
 
     const int lane = threadIdx.x & 31;
     const int lig = lane & (G - 1);
-    const long long gid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const int grp = (lane / G) & (NG - 1);
+    const long long gid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / TEAM;
     const long long total = (long long)a.n_chunks + a.n_light;
     const bool active = gid < total;
+    const Loader ld;
 
     int row = 0, beg = 0, end = 0, slot = -1;
     if (active)
@@ -159,28 +236,32 @@ __global__ void __launch_bounds__(256) row_pass_kernel(const PassArgs a)
     const T *L = static_cast<const T *>(a.L);
     const T *Y = static_cast<const T *>(a.Y);
 
-    float lrow[E], hrow[E], acc[E];
+    float lrow[E], hrow[TWO ? E : 1], acc[E];
 #pragma unroll
-    for (int e = 0; e < E; ++e) { lrow[e] = 0.f; hrow[e] = 0.f; acc[e] = 0.f; }
+    for (int e = 0; e < E; ++e) { lrow[e] = 0.f; acc[e] = 0.f; }
+#pragma unroll
+    for (int e = 0; e < (TWO ? E : 1); ++e) hrow[e] = 0.f;
     if (HAS_L && active)
-        load_row<T, R, true>(L + (size_t)row * R, lig, lrow);
-    if (MODE == M_BWD_ROW && active)
-        load_row_f32<T, R, true>(a.H + (size_t)row * R, lig, hrow);
+        team_load<T, VPL, G>(ld, L + (size_t)row * R, lig, lrow, false);
+    if constexpr (MODE == M_BWD_ROW)
+        if (active)
+            team_load_f32<T, VPL, G>(ld, a.H + (size_t)row * R, lig, hrow, false);
 
-    const int iters = (end - beg + U - 1) / U;
+    constexpr int PER = NG * U;
+    const int iters = (end - beg + PER - 1) / PER;
     const int witers = (int)__reduce_max_sync(0xffffffffu, (unsigned)iters);
 
     for (int it = 0; it < witers; ++it) {
-        const int p0 = beg + it * U;
+        const int p0 = beg + it * PER + grp;
         int jj[U], sidx[U];
         float sv[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int p = p0 + u;
+            const int p = p0 + u * NG;
             if (p < end) {
-                jj[u] = __ldg(a.col_idx + p);
-                sidx[u] = a.perm ? __ldg(a.perm + p) : p;
-                sv[u] = a.s ? __ldg(a.s + sidx[u]) : 1.f;
+                jj[u] = ld.idx(a.col_idx + p);
+                sidx[u] = a.perm ? ld.idx(a.perm + p) : p;
+                sv[u] = a.s ? ld.val(a.s + (a.s_direct ? p : sidx[u])) : 1.f;
             } else {
                 jj[u] = -1; sidx[u] = 0; sv[u] = 0.f;
             }
@@ -190,9 +271,9 @@ __global__ void __launch_bounds__(256) row_pass_kernel(const PassArgs a)
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             if (jj[u] >= 0) {
-                load_row<T, R, false>(Y + (size_t)jj[u] * R, lig, y[u]);
+                team_load<T, VPL, G>(ld, Y + (size_t)jj[u] * R, lig, y[u], true);
                 if constexpr (MODE == M_BWD_COL)
-                    load_row_f32<T, R, false>(a.H + (size_t)jj[u] * R, lig, h[u]);
+                    team_load_f32<T, VPL, G>(ld, a.H + (size_t)jj[u] * R, lig, h[u], true);
             } else {
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
@@ -262,11 +343,20 @@ __global__ void __launch_bounds__(256) row_pass_kernel(const PassArgs a)
         }
     }
 
-    if (ACC && active) {
-        float *dst = slot >= 0 ? a.partials + (size_t)slot * R
-                               : (a.out ? a.out + (size_t)row * R : nullptr);
-        if (dst)
-            store_row_f32<T, R>(dst, lig, acc);
+    if constexpr (ACC) {
+        // partial rows of the NG groups, summed in a fixed xor order
+#pragma unroll
+        for (int off = G; off < TEAM; off <<= 1) {
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+                acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], off);
+        }
+        if (active && grp == 0) {
+            float *dst = slot >= 0 ? a.partials + (size_t)slot * R
+                                   : (a.out ? a.out + (size_t)row * R : nullptr);
+            if (dst)
+                team_store_f32<T, VPL, G>(ld, dst, lig, acc);
+        }
     }
 }
 
@@ -313,7 +403,7 @@ __global__ void __launch_bounds__(256) row_pass_generic(const PassArgs a)
     for (int p = beg; p < end; ++p) {
         const int j = __ldg(a.col_idx + p);
         const int sidx = a.perm ? __ldg(a.perm + p) : p;
-        const float sv = a.s ? __ldg(a.s + sidx) : 1.f;
+        const float sv = a.s ? __ldg(a.s + (a.s_direct ? p : sidx)) : 1.f;
         const T *Yj = Y + (size_t)j * r;
         float d = 0.f, w = 0.f;
         if constexpr (MODE != M_SPMM) {
@@ -358,40 +448,79 @@ __global__ void __launch_bounds__(256) row_pass_generic(const PassArgs a)
     }
 }
 
-constexpr int unroll_cap(int mode, int E)
-{
-    return (mode == M_BWD_COL ? 32 : 64) / E;
-}
+// Kernel variants of the vectorised path: (VPL, NG, U) = vectors per lane,
+// groups per team, nonzeros per group per batch.  Variant 0 picks the
+// default of the row shape; the others are listed in kVariants.
+struct Variant {
+    int vpl, ng, u;
+};
 
-template <int MODE, typename T, int R, int U>
-cudaError_t launch_vec(const PassArgs &a, cudaStream_t st)
+template <int MODE, typename T, int R, int VPL, int NG, int U>
+cudaError_t launch_team(const PassArgs &a, cudaStream_t st)
 {
-    constexpr int G = Shape<T, R>::G;
+    constexpr int TEAM = TeamShape<T, R, VPL, NG>::TEAM;
     const long long total = (long long)a.n_chunks + a.n_light;
-    const long long threads = total * G;
-    const long long blocks = (threads + 255) / 256;
-    row_pass_kernel<MODE, T, R, U><<<(unsigned)blocks, 256, 0, st>>>(a);
+    const long long blocks = (total * TEAM + 255) / 256;
+    team_pass_kernel<MODE, T, R, VPL, NG, U><<<(unsigned)blocks, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int MODE, typename T, int R>
-cudaError_t dispatch_unroll(int unroll, const PassArgs &a, cudaStream_t st)
+// Whether (VPL, NG) is a valid team layout for rows of R elements of T.
+template <typename T, int R>
+constexpr bool team_ok(int V, int N)
 {
-    constexpr int CAP = unroll_cap(MODE, Shape<T, R>::E);
-    if (unroll >= 8 && CAP >= 8)
-        return launch_vec<MODE, T, R, 8>(a, st);
-    return launch_vec<MODE, T, R, 4>(a, st);
+    const int vecs = R * (int)sizeof(T) / 16;
+    if (V < 1 || vecs % V != 0) return false;
+    const int g = vecs / V;
+    return g >= 1 && (g & (g - 1)) == 0 && g * N <= 32 && 32 % (g * N) == 0;
+}
+
+// Register budget of a variant: the floats a lane keeps live (gathered rows
+// of a batch, local row, accumulator, gradient row) stay within 160.
+template <int MODE, typename T>
+constexpr bool fits_registers(int V, int U)
+{
+    const int E = V * (16 / (int)sizeof(T));
+    const int rows = U * (MODE == M_BWD_COL ? 2 : 1) + 2 + (MODE == M_BWD_ROW ? 1 : 0);
+    return E * rows <= 160;
+}
+
+// Minimum vectors per lane of a row shape (rows of more than 32 vectors
+// need several per lane).
+template <typename T, int R>
+constexpr int base_vpl() { return (R * (int)sizeof(T) / 16) > 32 ? (R * (int)sizeof(T) / 16) / 32 : 1; }
+
+template <int MODE, typename T, int R>
+cudaError_t dispatch_variant(int vpl, int ng, int u, const PassArgs &a, cudaStream_t st)
+{
+    constexpr int B = base_vpl<T, R>();
+#define FMM_TRY_VARIANT(V, N, UU)                                                   \
+    if constexpr (team_ok<T, R>(V, N) && fits_registers<MODE, T>(V, UU)) {          \
+        if (vpl == V && ng == N && u == UU)                                         \
+            return launch_team<MODE, T, R, V, N, UU>(a, st);                        \
+    }
+    FMM_TRY_VARIANT(B, 1, 4)
+    FMM_TRY_VARIANT(B, 1, 8)
+    FMM_TRY_VARIANT(2 * B, 2, 2)
+    FMM_TRY_VARIANT(2 * B, 2, 4)
+    FMM_TRY_VARIANT(4 * B, 4, 1)
+    FMM_TRY_VARIANT(4 * B, 4, 2)
+    FMM_TRY_VARIANT(2 * B, 1, 4)
+    FMM_TRY_VARIANT(B, 2, 4)
+#undef FMM_TRY_VARIANT
+    // a variant that does not fit this row shape: one group per row
+    return launch_team<MODE, T, R, B, 1, 8>(a, st);
 }
 
 template <typename T, int R>
-cudaError_t dispatch_mode(int mode, int unroll, const PassArgs &a, cudaStream_t st)
+cudaError_t dispatch_mode(int mode, int vpl, int ng, int u, const PassArgs &a, cudaStream_t st)
 {
     switch (mode) {
-    case M_FUSED: return dispatch_unroll<M_FUSED, T, R>(unroll, a, st);
-    case M_SDDMM: return dispatch_unroll<M_SDDMM, T, R>(unroll, a, st);
-    case M_SPMM: return dispatch_unroll<M_SPMM, T, R>(unroll, a, st);
-    case M_BWD_ROW: return dispatch_unroll<M_BWD_ROW, T, R>(unroll, a, st);
-    case M_BWD_COL: return dispatch_unroll<M_BWD_COL, T, R>(unroll, a, st);
+    case M_FUSED: return dispatch_variant<M_FUSED, T, R>(vpl, ng, u, a, st);
+    case M_SDDMM: return dispatch_variant<M_SDDMM, T, R>(vpl, ng, u, a, st);
+    case M_SPMM: return dispatch_variant<M_SPMM, T, R>(vpl, ng, u, a, st);
+    case M_BWD_ROW: return dispatch_variant<M_BWD_ROW, T, R>(vpl, ng, u, a, st);
+    case M_BWD_COL: return dispatch_variant<M_BWD_COL, T, R>(vpl, ng, u, a, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -412,8 +541,9 @@ cudaError_t launch_generic(int mode, const PassArgs &a, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// vpl is given in multiples of the shape's minimum (1, 2 or 4).
 template <typename T>
-cudaError_t launch_pass_typed(int mode, int unroll, bool vec, const PassArgs &a,
+cudaError_t launch_pass_typed(int mode, int vpl_mult, int ng, int u, bool vec, const PassArgs &a,
                               cudaStream_t st)
 {
     const long long total = (long long)a.n_chunks + a.n_light;
@@ -421,10 +551,10 @@ cudaError_t launch_pass_typed(int mode, int unroll, bool vec, const PassArgs &a,
         return cudaSuccess;
     if (vec) {
         switch (a.r) {
-        case 32: return dispatch_mode<T, 32>(mode, unroll, a, st);
-        case 64: return dispatch_mode<T, 64>(mode, unroll, a, st);
-        case 128: return dispatch_mode<T, 128>(mode, unroll, a, st);
-        case 256: return dispatch_mode<T, 256>(mode, unroll, a, st);
+        case 32: return dispatch_mode<T, 32>(mode, vpl_mult * base_vpl<T, 32>(), ng, u, a, st);
+        case 64: return dispatch_mode<T, 64>(mode, vpl_mult * base_vpl<T, 64>(), ng, u, a, st);
+        case 128: return dispatch_mode<T, 128>(mode, vpl_mult * base_vpl<T, 128>(), ng, u, a, st);
+        case 256: return dispatch_mode<T, 256>(mode, vpl_mult * base_vpl<T, 256>(), ng, u, a, st);
         default: break;
         }
     }

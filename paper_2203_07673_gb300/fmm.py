@@ -56,7 +56,7 @@ class _Csr(ctypes.Structure):
 
 class _Options(ctypes.Structure):
     _fields_ = [("flags", ctypes.c_uint32), ("split_nnz", ctypes.c_int32),
-                ("unroll", ctypes.c_int32)]
+                ("variant", ctypes.c_int32)]
 
 
 class _Info(ctypes.Structure):
@@ -65,8 +65,8 @@ class _Info(ctypes.Structure):
                 ("max_row_nnz", ctypes.c_int32), ("max_col_nnz", ctypes.c_int32),
                 ("split_rows", ctypes.c_int32), ("split_cols", ctypes.c_int32),
                 ("row_chunks", ctypes.c_int32), ("col_chunks", ctypes.c_int32),
-                ("split_nnz", ctypes.c_int32), ("unroll", ctypes.c_int32),
-                ("workspace_bytes", ctypes.c_int64)]
+                ("split_nnz", ctypes.c_int32), ("variant", ctypes.c_int32),
+                ("variant_t", ctypes.c_int32), ("workspace_bytes", ctypes.c_int64)]
 
 
 _lock = threading.Lock()
@@ -143,7 +143,7 @@ class Plan:
 
     def __init__(self, row_ptr: torch.Tensor, col_idx: torch.Tensor, n: int, r: int,
                  dtype=torch.float32, transpose: bool = True, split_nnz: int = 0,
-                 unroll: int = 0, stream=None):
+                 variant: int = 0, stream=None):
         if dtype not in _DT:
             raise TypeError(f"unsupported dtype {dtype}")
         self.handle = None
@@ -158,7 +158,7 @@ class Plan:
         self.dtype = dtype
         csr = _Csr(self.m, self.n, self.nnz, row_ptr.data_ptr(),
                    col_idx.data_ptr() if self.nnz else None)
-        opt = _Options(0 if transpose else FMM_PLAN_NO_TRANSPOSE, int(split_nnz), int(unroll))
+        opt = _Options(0 if transpose else FMM_PLAN_NO_TRANSPOSE, int(split_nnz), int(variant))
         out = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             rc = lib().fmm_plan_create(ctypes.byref(csr), self.r, _DT[dtype], ctypes.byref(opt),

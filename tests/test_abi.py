@@ -72,7 +72,10 @@ def test_host_side_argument_errors(fmm_lib):
                                ctypes.byref(out)) == fmm_lib.FMM_EUNSUPPORTED
     assert lib.fmm_plan_create(ctypes.byref(csr), 8, 7, None, None,
                                ctypes.byref(out)) == fmm_lib.FMM_EUNSUPPORTED
-    opt = fmm_lib._Options(0, 0, 3)
+    opt = fmm_lib._Options(0, 0, 333)
+    assert lib.fmm_plan_create(ctypes.byref(csr), 8, 0, ctypes.byref(opt), None,
+                               ctypes.byref(out)) == fmm_lib.FMM_EINVAL
+    opt = fmm_lib._Options(0, -1, 0)
     assert lib.fmm_plan_create(ctypes.byref(csr), 8, 0, ctypes.byref(opt), None,
                                ctypes.byref(out)) == fmm_lib.FMM_EINVAL
     assert lib.fmm_plan_create(ctypes.byref(csr), 8, 0, None, None, None) == fmm_lib.FMM_EINVAL

@@ -100,11 +100,13 @@ def test_parity_all_ops(kind, r, dtype):
     run_all(S, opts, r, dtype, seed=r, check_bf16_vs_f32=(dtype == torch.bfloat16))
 
 
-@pytest.mark.parametrize("unroll", [4, 8])
-@pytest.mark.parametrize("split_nnz", [16, 100, 0])
-def test_schedule_options(unroll, split_nnz):
+@pytest.mark.parametrize("variant", [114, 118, 222, 224, 441, 442, 214, 124])
+@pytest.mark.parametrize("split_nnz", [16, 0])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16], ids=["f32", "bf16"])
+@pytest.mark.parametrize("r", [32, 128, 256])
+def test_kernel_variants(r, dtype, split_nnz, variant):
     S, _ = pattern("hubs", 7)
-    run_all(S, {"split_nnz": split_nnz, "unroll": unroll}, 64, torch.float32, seed=3)
+    run_all(S, {"split_nnz": split_nnz, "variant": variant}, r, dtype, seed=3)
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16], ids=["f32", "bf16"])
