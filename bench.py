@@ -50,10 +50,45 @@ def kernel_source_sha() -> str:
 
 
 def gather_model_bytes(m, nnz, r, e, vals=True):
-    """Algorithmic bytes of one FusedMM call: the CSR (row_ptr, col_idx,
+    """Algorithmic bytes of one FusedMM row pass: the CSR (row_ptr, col_idx,
     values), each local row read once (rows x r x e), one dense row gathered
     per nonzero (nnz x r x e) and the float32 output written once."""
     return 4 * (m + 1) + 4 * nnz + (4 * nnz if vals else 0) + m * r * e + nnz * r * e + 4 * m * r
+
+
+def permute_bytes(nnz):
+    """Values of S into S^T order: perm read, one value fetched, one written."""
+    return 12 * nnz
+
+
+def step_calls(k, S, r, e, vals_given):
+    """(name, model bytes) of the calls of one step of workload k."""
+    m, n, nnz = S.m, S.n, S.nnz
+    fwd = gather_model_bytes(m, nnz, r, e, vals_given)
+    fwd_t = gather_model_bytes(n, nnz, r, e, vals_given) + (permute_bytes(nnz) if vals_given else 0)
+    if k == 3:
+        # backward: pass over S (A_i, G_i local, B_j gathered, dA and ds written),
+        # pass over S^T (B_j local, A_i and G_i gathered, dB written)
+        p1 = gather_model_bytes(m, nnz, r, e, True) + 4 * m * r + 4 * nnz
+        p2 = gather_model_bytes(n, nnz, r, e, True) + 4 * nnz * r + permute_bytes(nnz)
+        return [("fmm_fusedmm", fwd), ("fmm_fusedmm_bwd", p1 + p2)]
+    return [("fmm_fusedmm", fwd), ("fmm_fusedmm_t", fwd_t)]
+
+
+def reduce_max(values, device, world):
+    """Element-wise maximum of a list of floats over all ranks."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def whole_job_value(units_per_step_per_rank, steps, world, max_elapsed_ms):
+    """Units all ranks processed divided by the slowest rank's time (per s)."""
+    return units_per_step_per_rank * steps * world / (max_elapsed_ms / 1e3)
 
 
 def load_peaks():
@@ -120,7 +155,9 @@ class ClockSampler:
 
 def make_workload(k: int, scale: float):
     from paper_2203_07673_gb300 import workloads as wl
-    return wl.workload(k, scale_rows=scale)
+    w = wl.workload(k, scale_rows=scale)
+    w["k"] = k
+    return w
 
 
 # --------------------------------------------------------------- oracle leg
@@ -141,11 +178,16 @@ def oracle_sample(w, seconds: float, rows_hint: int | None = None):
         v = None if vals is None else vals[:sub_s.nnz]
         return sub_s.row_ptr, ci.astype(np.int64), v, A[:rows], B[cols], len(cols), sub_s.nnz
 
+    fwd_bwd = w.get("k") == 3
+
     def run(rows):
         rp, ci, v, a, b, n, nnz = sub(rows)
         t0 = time.perf_counter()
         oracle.fusedmm(rp, ci, v, a, b, n)
-        oracle.fusedmm_t(rp, ci, v, a, b, n)
+        if fwd_bwd:
+            oracle.fusedmm_grad(rp, ci, v if v is not None else np.ones(nnz), a, b, a, n)
+        else:
+            oracle.fusedmm_t(rp, ci, v, a, b, n)
         return time.perf_counter() - t0, nnz, n
 
     rows = rows_hint or min(S.m, 1024)
@@ -154,11 +196,12 @@ def oracle_sample(w, seconds: float, rows_hint: int | None = None):
         rows = int(min(S.m, max(rows, rows * seconds / max(t, 1e-6))))
         t, nnz, ncols = run(rows)
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    what = ("FusedMMA forward (rows on {t} OpenMP threads) + its gradient (sequential)"
+            if fwd_bwd else "FusedMMA (rows on {t} OpenMP threads) + FusedMMB (sequential scatter)")
     desc = (f"first {rows} of {S.m} rows ({nnz} nnz, {nnz / max(S.nnz, 1):.2%} of the "
             f"workload), columns remapped to the {ncols} they touch; "
-            f"FusedMMA + FusedMMB in FP64 (oracle/fmm_oracle.c); FusedMMA rows on "
-            f"{threads} OpenMP threads, the FusedMMB scatter on 1")
-    return 2.0 * nnz * r / t, desc, threads, rows
+            + what.format(t=threads) + " in FP64 (oracle/fmm_oracle.c)")
+    return (1.0 if fwd_bwd else 2.0) * nnz * r / t, desc, threads, rows
 
 
 def _bf16_round(x):
@@ -166,9 +209,61 @@ def _bf16_round(x):
     return torch.from_numpy(x).to(torch.bfloat16).double().numpy()
 
 
+def batched_oracle_step(mats, seconds):
+    """FP64 oracle FusedMMA + gradient over the batched matrices in order
+    until `seconds` of CPU time; returns (units per second, matrices used)."""
+    import oracle
+    units, spent, used = 0.0, 0.0, 0
+    for m in mats:
+        if spent >= seconds:
+            break
+        S, r = m["S"], m["r"]
+        a = _bf16_round(m["A"]); b = _bf16_round(m["B"])
+        v = m["vals"].astype(np.float64)
+        t0 = time.perf_counter()
+        oracle.fusedmm(S.row_ptr, S.col_idx, v, a, b, S.n)
+        oracle.fusedmm_grad(S.row_ptr, S.col_idx, v, a, b, a, S.n)
+        spent += time.perf_counter() - t0
+        units += S.nnz * r
+        used += 1
+    return units / spent, used
+
+
+def run_reference_batched(args):
+    from paper_2203_07673_gb300 import workloads as wl
+    specs = wl.batched_specs(args.batch_count, scale_rows=args.scale)
+    mats = []
+    for t, sp in enumerate(specs[:64]):
+        mats.append(wl.batched_matrix(sp, t))
+    for _ in range(args.warmup):
+        batched_oracle_step(mats, 0.5)
+    vals, used = [], 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, used = batched_oracle_step(mats, 1.0)
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    value = float(np.median(vals))
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    desc = (f"the first {used} of {len(specs)} batched matrices (numpy-drawn, same recipe), "
+            f"FusedMMA (rows on {threads} OpenMP threads) + its gradient (sequential) in FP64")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wl.WORKLOADS[5]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
+    if args.workload == 5:
+        return run_reference_batched(args)
     w = make_workload(args.workload, args.scale)
     # calibrate one step to about 1 s of CPU work, then time W + K steps
     _, _, _, rows = oracle_sample(w, 1.0)
@@ -196,8 +291,10 @@ def run_reference(args, rank, world):
 
 def workload_config(w, args):
     S = w["S"]
+    step = ("FusedMMA forward + backward (dA, dB, ds); units = nnz*r per step"
+            if args.workload == 3 else "FusedMMA + FusedMMB; units = 2*nnz*r per step")
     return {"workload": w["name"], "m": S.m, "n": S.n, "nnz": S.nnz, "r": w["r"],
-            "input_dtype": w["dtype"], "step": "FusedMMA + FusedMMB",
+            "input_dtype": w["dtype"], "step": step,
             "l2": "not flushed: A and B are larger than L2" if S.m * w["r"] * 4 > 2**28
             else "L2-resident inputs", "parallelism": f"replicas x{args.gpus}",
             "scale_rows": args.scale}
@@ -214,12 +311,16 @@ def run_fmm(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     w = make_workload(args.workload, args.scale)
-    S, r = w["S"], w["r"]
+    S, r, k = w["S"], w["r"], args.workload
     tdt = torch.float32 if w["dtype"] == "f32" else torch.bfloat16
     e = 4 if w["dtype"] == "f32" else 2
     rp = torch.from_numpy(S.row_ptr).to(dev)
     ci = torch.from_numpy(S.col_idx).to(dev)
-    vals = None if w["vals"] is None else torch.from_numpy(w["vals"]).to(dev)
+    if k == 3:
+        # s = 1 with a gradient wanted: the values are an explicit ones vector
+        vals = torch.ones(S.nnz, device=dev)
+    else:
+        vals = None if w["vals"] is None else torch.from_numpy(w["vals"]).to(dev)
     A = torch.from_numpy(w["A"]).to(dev).to(tdt).contiguous()
     B = torch.from_numpy(w["B"]).to(dev).to(tdt).contiguous()
     plan = fmm.Plan(rp, ci, S.n, r, tdt)
@@ -227,11 +328,29 @@ def run_fmm(args, rank, world, local_rank):
     out = torch.empty(S.m, r, device=dev)
     out_t = torch.empty(S.n, r, device=dev)
     v = torch.empty(S.nnz, device=dev)
+    G = None
+    if k == 3:
+        G = torch.from_numpy(w["A"].astype(np.float32)).to(dev)   # a fixed upstream gradient
+        dA = torch.empty(S.m, r, device=dev)
+        dB = torch.empty(S.n, r, device=dev)
+        ds = torch.empty(S.nnz, device=dev)
     stream = torch.cuda.current_stream()
+    lib = fmm.lib()
+    sp = stream.cuda_stream
 
-    def step():
+    def call_fwd():
         fmm.fusedmm(plan, vals, A, B, out=out)
-        fmm.fusedmm_t(plan, vals, A, B, out=out_t)
+
+    def call_second():
+        if k == 3:
+            rc = lib.fmm_fusedmm_bwd(plan.handle, vals.data_ptr(), A.data_ptr(), B.data_ptr(),
+                                     G.data_ptr(), dA.data_ptr(), dB.data_ptr(), ds.data_ptr(), sp)
+            fmm._check(rc, "fmm_fusedmm_bwd")
+        else:
+            fmm.fusedmm_t(plan, vals, A, B, out=out_t)
+
+    calls = step_calls(k, S, r, e, vals is not None)
+    fns = [call_fwd, call_second]
 
     def barrier():
         if world > 1:
@@ -239,106 +358,112 @@ def run_fmm(args, rank, world, local_rank):
         torch.cuda.synchronize()
 
     for _ in range(args.warmup):
-        step()
+        for f in fns:
+            f()
     barrier()
 
     clocks = ClockSampler(local_rank)
     clocks.start()
     K = args.steps
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(fns) + 1)] for _ in range(K)]
     barrier()
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     t_start.record(stream)
-    for k in range(K):
-        ev[k][0].record(stream)
-        fmm.fusedmm(plan, vals, A, B, out=out)
-        ev[k][1].record(stream)
-        fmm.fusedmm_t(plan, vals, A, B, out=out_t)
-        ev[k][2].record(stream)
+    for kk in range(K):
+        ev[kk][0].record(stream)
+        for c, f in enumerate(fns):
+            f()
+            ev[kk][c + 1].record(stream)
     t_end.record(stream)
     barrier()
     clk = clocks.stop()
     elapsed_ms = t_start.elapsed_time(t_end)
-    fwd_ms = float(np.mean([ev[k][0].elapsed_time(ev[k][1]) for k in range(K)]))
-    fwd_t_ms = float(np.mean([ev[k][1].elapsed_time(ev[k][2]) for k in range(K)]))
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    call_ms = [float(np.mean([ev[kk][c].elapsed_time(ev[kk][c + 1]) for kk in range(K)]))
+               for c in range(len(fns))]
+    elapsed_ms = reduce_max([elapsed_ms], dev, world)[0]
 
-    # unfused path (SDDMM writes v, SpMM reads it back), same inputs
+    # unfused path on the same inputs (SDDMM writes v, SpMM reads it back)
     def unfused():
         fmm.sddmm(plan, vals, A, B, out=v)
         fmm.spmm(plan, v, B, out=out)
-        fmm.sddmm(plan, vals, A, B, out=v)
-        fmm.spmm_t(plan, v, A, out=out_t)
+        if k != 3:
+            fmm.sddmm(plan, vals, A, B, out=v)
+            fmm.spmm_t(plan, v, A, out=out_t)
 
-    for _ in range(max(1, args.warmup)):
-        unfused()
-    barrier()
-    u0 = torch.cuda.Event(enable_timing=True); u1 = torch.cuda.Event(enable_timing=True)
-    u0.record(stream)
-    for _ in range(K):
-        unfused()
-    u1.record(stream)
-    barrier()
-    unfused_ms = u0.elapsed_time(u1) / K
+    def fused_only():
+        fmm.fusedmm(plan, vals, A, B, out=out)
+        if k != 3:
+            fmm.fusedmm_t(plan, vals, A, B, out=out_t)
+
+    def timed(fn, reps):
+        for _ in range(max(3, min(args.warmup, 5))):
+            fn()
+        barrier()
+        a0 = torch.cuda.Event(enable_timing=True); a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(reps):
+            fn()
+        a1.record(stream)
+        barrier()
+        return a0.elapsed_time(a1) / reps
+
+    reps = max(3, min(K, 50))
+    unfused_ms = timed(unfused, reps)
+    fused_ms = timed(fused_only, reps)
 
     # end to end through the public API from pinned host buffers
     A_h = torch.from_numpy(w["A"]).to(tdt).pin_memory()
     B_h = torch.from_numpy(w["B"]).to(tdt).pin_memory()
-    vals_h = None if w["vals"] is None else torch.from_numpy(w["vals"]).pin_memory()
+    vals_h = None if vals is None else vals.cpu().pin_memory()
     out_h = torch.empty(S.m, r).pin_memory()
-    out_t_h = torch.empty(S.n, r).pin_memory()
+    second_h = torch.empty(S.n, r).pin_memory()
+    G_h = None if G is None else G.cpu().pin_memory()
+    dA_h = None if G is None else torch.empty(S.m, r).pin_memory()
+    ds_h = None if G is None else torch.empty(S.nnz).pin_memory()
 
     def e2e_step():
         A.copy_(A_h, non_blocking=True)
         B.copy_(B_h, non_blocking=True)
         if vals is not None:
             vals.copy_(vals_h, non_blocking=True)
-        fmm.fusedmm(plan, vals, A, B, out=out)
-        fmm.fusedmm_t(plan, vals, A, B, out=out_t)
+        if G is not None:
+            G.copy_(G_h, non_blocking=True)
+        for f in fns:
+            f()
         out_h.copy_(out, non_blocking=True)
-        out_t_h.copy_(out_t, non_blocking=True)
+        second_h.copy_(dB if k == 3 else out_t, non_blocking=True)
+        if G is not None:
+            dA_h.copy_(dA, non_blocking=True)
+            ds_h.copy_(ds, non_blocking=True)
 
-    for _ in range(max(1, min(args.warmup, 3))):
-        e2e_step()
-    barrier()
-    k_e2e = max(1, min(K, 50))
-    x0 = torch.cuda.Event(enable_timing=True); x1 = torch.cuda.Event(enable_timing=True)
-    x0.record(stream)
-    for _ in range(k_e2e):
-        e2e_step()
-    x1.record(stream)
-    barrier()
-    e2e_ms = x0.elapsed_time(x1) / k_e2e
-    if world > 1:
-        t = torch.tensor([unfused_ms, e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        unfused_ms, e2e_ms = (float(x) for x in t.tolist())
+    e2e_ms = timed(e2e_step, max(3, min(K, 30)))
+    unfused_ms, fused_ms, e2e_ms = reduce_max([unfused_ms, fused_ms, e2e_ms], dev, world)
 
-    units_step = 2.0 * S.nnz * r
-    value = units_step * K * world / (elapsed_ms / 1e3)
+    units_step = (1.0 if k == 3 else 2.0) * S.nnz * r
+    value = whole_job_value(units_step, K, world, elapsed_ms)
     ms_per_step = elapsed_ms / K
     peak, peak_kind = load_peaks()
-    alg = gather_model_bytes(S.m, S.nnz, r, e, vals is not None)
-    achieved = alg / (fwd_ms / 1e3) / 1e9
+    dom = int(np.argmax(call_ms))
+    dom_name, dom_bytes = calls[dom]
+    achieved = dom_bytes / (call_ms[dom] / 1e3) / 1e9
     traffic, traffic_note = None, "no ncu capture for the current kernel source"
     try:
         with open(PROFILE_TRAFFIC) as fh:
             prof = json.load(fh)
-        if (prof.get("source_sha1") == kernel_source_sha()
-                and prof.get("workload") == w["name"]):
-            traffic = float(prof["dram_bytes_per_launch"])
-            traffic_note = prof.get("note", "")
+        entry = prof.get(f"{w['name']}|{dom_name}|{w['dtype']}")
+        if entry and entry.get("source_sha1") == kernel_source_sha():
+            traffic = float(entry["dram_bytes_per_call"])
+            traffic_note = entry.get("note", "")
     except Exception:
         pass
-    launches_per_call = 1 + (1 if info["split_rows"] else 0)
-    launches_per_call_t = 1 + (1 if info["split_cols"] else 0) + (1 if vals is not None else 0)
+    launches = {"fmm_fusedmm": 1 + (1 if info["split_rows"] else 0),
+                "fmm_fusedmm_t": 1 + (1 if info["split_cols"] else 0) + (1 if vals is not None else 0),
+                "fmm_fusedmm_bwd": 3 + (1 if info["split_rows"] else 0) + (1 if info["split_cols"] else 0)}
     h2d = A_h.numel() * A_h.element_size() + B_h.numel() * B_h.element_size() + (
-        0 if vals_h is None else vals_h.numel() * 4)
-    d2h = (out_h.numel() + out_t_h.numel()) * 4
+        0 if vals_h is None else vals_h.numel() * 4) + (0 if G_h is None else G_h.numel() * 4)
+    d2h = (out_h.numel() + second_h.numel()) * 4 + (
+        0 if G is None else (dA_h.numel() + ds_h.numel()) * 4)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
@@ -346,27 +471,37 @@ def run_fmm(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_config(w, args),
         "roofline": {
-            "bound": "hbm", "kernel": "row_pass_kernel<M_FUSED> (fmm_fusedmm)",
+            "bound": "hbm", "kernel": dom_name,
             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic, "peak_kind": f"{peak_kind} copy bandwidth",
-            "algorithmic_bytes_per_launch": alg,
+            "traffic": traffic, "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+            "algorithmic_bytes_per_call": dom_bytes,
             "bytes_model": "gather model: CSR + local rows once + one dense row per nonzero "
-                           "+ float32 output once",
-            "kernel_ms": fwd_ms,
-            "dram_frac": None if traffic is None else traffic / (fwd_ms / 1e3) / 1e9 / peak,
+                           "+ float32 outputs once (+ value permutation on the S^T side)",
+            "call_ms": call_ms[dom],
+            "dram_frac": None if traffic is None else traffic / (call_ms[dom] / 1e3) / 1e9 / peak,
             "traffic_note": traffic_note,
         },
-        "fused": {"fusedmm_ms": fwd_ms, "fusedmm_t_ms": fwd_t_ms,
-                  "unfused_ms_per_step": unfused_ms,
-                  "fused_speedup_vs_unfused": unfused_ms / ms_per_step},
+        "calls": {name: {"ms": call_ms[c], "model_bytes": b,
+                         "model_GBs": b / (call_ms[c] / 1e3) / 1e9}
+                  for c, (name, b) in enumerate(calls)},
+        "fused_vs_unfused": None if k == 3 else {
+            "fused_ms": fused_ms, "unfused_ms": unfused_ms,
+            "speedup": unfused_ms / fused_ms,
+            "unfused": "fmm_sddmm + fmm_spmm + fmm_sddmm + fmm_spmm_t"},
         "e2e": {"value": units_step * world / (e2e_ms / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
-        "gpu_launches": K * (launches_per_call + launches_per_call_t),
+        "gpu_launches": K * sum(launches[name] for name, _ in calls),
         "clocks": clk,
-        "plan": {k: info[k] for k in ("max_row_nnz", "max_col_nnz", "split_rows",
-                                      "split_cols", "variant", "variant_t",
-                                      "workspace_bytes")},
+        "plan": {kk: info[kk] for kk in ("max_row_nnz", "max_col_nnz", "split_rows",
+                                         "split_cols", "variant", "variant_t",
+                                         "workspace_bytes")},
     }
+    if k == 3:
+        line["fused_vs_unfused"] = {"fused_fwd_ms": fused_ms, "unfused_fwd_ms": unfused_ms,
+                                    "speedup": unfused_ms / fused_ms,
+                                    "unfused": "fmm_sddmm + fmm_spmm"}
+    if w["dtype"] == "bf16":
+        line["dtype"] = "f32 (bf16 inputs)"
     if rank == 0 and not args.no_cpu_baseline:
         cv, desc, threads, _ = oracle_sample(w, args.cpu_seconds)
         line["cpu_baseline"] = {"value": cv, "unit": UNIT, "cores": threads, "kind": "oracle",
@@ -377,13 +512,208 @@ def run_fmm(args, rank, world, local_rank):
     return 0
 
 
+def run_batched(args, rank, world, local_rank):
+    """Workload 5: 512 uneven matrices, BF16 inputs, forward + backward as one
+    persistent launch each (fmm_batch_forward / fmm_batch_backward), replayed
+    from CUDA graphs; variants picked by the autotuner per shape group."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2203_07673_gb300 import autotune, fmm
+    from paper_2203_07673_gb300 import workloads as wl
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    specs = wl.batched_specs(args.batch_count, scale_rows=args.scale)
+    t0 = time.perf_counter()
+    items, mats = [], []
+    for t, sp in enumerate(specs):
+        m = wl.batched_matrix_torch(sp, t, dev)
+        r = m["r"]
+        plan = fmm.Plan(m["row_ptr"], m["col_idx"], m["n"], r, torch.bfloat16,
+                        split_nnz=1 << 30)
+        g = torch.Generator(device=dev)
+        g.manual_seed(7919 * t + 1)
+        items.append(dict(plan=plan, vals=m["vals"], A=m["A"].bfloat16().contiguous(),
+                          B=m["B"].bfloat16().contiguous(),
+                          G=torch.randn(m["m"], r, device=dev, generator=g),
+                          out=torch.empty(m["m"], r, device=dev),
+                          dA=torch.empty(m["m"], r, device=dev),
+                          dB=torch.empty(m["n"], r, device=dev),
+                          ds=torch.empty(m["col_idx"].numel(), device=dev),
+                          rp=m["row_ptr"], ci=m["col_idx"]))
+        mats.append(m)
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    tuned = autotune.tune_batch(items) if not args.no_tune else {}
+    tune_s = time.perf_counter() - t0
+    keys = ("plan", "vals", "A", "B", "out", "G", "dA", "dB", "ds")
+    batch = fmm.Batch([{k: it[k] for k in keys} for it in items])
+    stream = torch.cuda.current_stream()
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        batch.forward(); batch.backward()
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    g_fwd, g_bwd = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g_fwd):
+        batch.forward()
+    with torch.cuda.graph(g_bwd):
+        batch.backward()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        g_fwd.replay(); g_bwd.replay()
+    barrier()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    barrier()
+    t_s = torch.cuda.Event(enable_timing=True); t_e = torch.cuda.Event(enable_timing=True)
+    t_s.record(stream)
+    for kk in range(K):
+        ev[kk][0].record(stream)
+        g_fwd.replay()
+        ev[kk][1].record(stream)
+        g_bwd.replay()
+        ev[kk][2].record(stream)
+    t_e.record(stream)
+    barrier()
+    clk = clocks.stop()
+    elapsed_ms = t_s.elapsed_time(t_e)
+    fwd_ms = float(np.mean([ev[kk][0].elapsed_time(ev[kk][1]) for kk in range(K)]))
+    bwd_ms = float(np.mean([ev[kk][1].elapsed_time(ev[kk][2]) for kk in range(K)]))
+    elapsed_ms = reduce_max([elapsed_ms], dev, world)[0]
+
+    def timed(fn, reps=3):
+        fn()
+        barrier()
+        a0 = torch.cuda.Event(enable_timing=True); a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(reps):
+            fn()
+        a1.record(stream)
+        barrier()
+        return a0.elapsed_time(a1) / reps
+
+    v_bufs = [torch.empty(it["ci"].numel(), device=dev) for it in items]
+
+    def per_matrix_fused():
+        for it in items:
+            fmm.fusedmm(it["plan"], it["vals"], it["A"], it["B"], out=it["out"])
+
+    def per_matrix_unfused():
+        for it, v in zip(items, v_bufs):
+            fmm.sddmm(it["plan"], it["vals"], it["A"], it["B"], out=v)
+            fmm.spmm(it["plan"], v, it["B"], out=it["out"])
+
+    loop_fused_ms = timed(per_matrix_fused)
+    loop_unfused_ms = timed(per_matrix_unfused)
+
+    # end to end: inputs from pinned host memory, outputs back, every step
+    host_in = [(it[k].cpu().pin_memory(), it[k]) for it in items for k in ("vals", "A", "B", "G")]
+    host_out = [(torch.empty(it[k].shape).pin_memory(), it[k]) for it in items
+                for k in ("out", "dA", "dB", "ds")]
+
+    def e2e_step():
+        for h, d in host_in:
+            d.copy_(h, non_blocking=True)
+        g_fwd.replay(); g_bwd.replay()
+        for h, d in host_out:
+            h.copy_(d, non_blocking=True)
+
+    e2e_ms = timed(e2e_step, 2)
+    h2d = sum(h.numel() * h.element_size() for h, _ in host_in)
+    d2h = sum(h.numel() * h.element_size() for h, _ in host_out)
+
+    nnz = [it["ci"].numel() for it in items]
+    rs = [it["plan"].r for it in items]
+    units_step = float(sum(z * r for z, r in zip(nnz, rs)))
+    value = whole_job_value(units_step, K, world, elapsed_ms)
+    fwd_bytes = sum(gather_model_bytes(it["plan"].m, z, r, 2, True) for it, z, r in zip(items, nnz, rs))
+    bwd_bytes = sum(gather_model_bytes(it["plan"].m, z, r, 2, True) + 4 * it["plan"].m * r + 4 * z
+                    + gather_model_bytes(it["plan"].n, z, r, 2, True) + 4 * z * r + 4 * z
+                    for it, z, r in zip(items, nnz, rs))
+    peak, peak_kind = load_peaks()
+    dom_ms, dom_bytes, dom_name = (bwd_ms, bwd_bytes, "batch_kernel<bf16, backward>") \
+        if bwd_ms >= fwd_ms else (fwd_ms, fwd_bytes, "batch_kernel<bf16, forward>")
+    achieved = dom_bytes / (dom_ms / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": elapsed_ms / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (bf16 inputs)",
+        "data": "synthetic",
+        "config": {"workload": wl.WORKLOADS[5], "matrices": len(items), "rows": int(sum(
+            it["plan"].m for it in items)), "nnz": int(sum(nnz)), "r_mix": {
+            str(r): rs.count(r) for r in (32, 64, 128)},
+            "step": "batched FusedMMA forward + backward (dA, dB, ds), one persistent launch "
+                    "each, replayed from CUDA graphs; units = sum nnz*r per step",
+            "l2": "not flushed: the batch's operands total several GB",
+            "parallelism": f"replicas x{args.gpus}", "scale_rows": args.scale},
+        "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                     "algorithmic_bytes_per_call": dom_bytes, "call_ms": dom_ms,
+                     "bytes_model": "gather model summed over the matrices"},
+        "calls": {"batch_forward": {"ms": fwd_ms, "model_bytes": fwd_bytes,
+                                    "model_GBs": fwd_bytes / (fwd_ms / 1e3) / 1e9},
+                  "batch_backward": {"ms": bwd_ms, "model_bytes": bwd_bytes,
+                                     "model_GBs": bwd_bytes / (bwd_ms / 1e3) / 1e9}},
+        "batching": {"per_matrix_fused_forward_ms": loop_fused_ms,
+                     "per_matrix_unfused_forward_ms": loop_unfused_ms,
+                     "batched_forward_ms": fwd_ms,
+                     "speedup_vs_per_matrix_fused": loop_fused_ms / fwd_ms,
+                     "speedup_vs_per_matrix_unfused": loop_unfused_ms / fwd_ms},
+        "e2e": {"value": units_step * world / (e2e_ms / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "gpu_launches": 2 * K,
+        "clocks": clk,
+        "setup": {"generate_s": gen_s, "autotune_s": tune_s, "tuned_groups": len(tuned)},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        done_units, t_cpu, used = 0.0, 0.0, 0
+        for it, m in zip(items, mats):
+            if t_cpu >= args.cpu_seconds:
+                break
+            rp = m["row_ptr"].cpu().numpy(); ci = m["col_idx"].cpu().numpy()
+            a = it["A"].double().cpu().numpy(); b = it["B"].double().cpu().numpy()
+            v = m["vals"].double().cpu().numpy(); g_ = it["G"].double().cpu().numpy()
+            c0 = time.perf_counter()
+            oracle.fusedmm(rp, ci, v, a, b, m["n"])
+            oracle.fusedmm_grad(rp, ci, v, a, b, g_, m["n"])
+            t_cpu += time.perf_counter() - c0
+            done_units += ci.size * m["r"]
+            used += 1
+        threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+        line["cpu_baseline"] = {
+            "value": done_units / t_cpu, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"the first {used} of {len(items)} matrices, FusedMMA (rows on {threads} "
+                      "OpenMP threads) + its gradient (sequential) in FP64 on the BF16-rounded "
+                      "inputs (oracle/fmm_oracle.c)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    batch.close()
+    for it in items:
+        it["plan"].close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["fmm", "reference"], default="fmm")
-    ap.add_argument("--workload", type=int, default=2, choices=[1, 2, 3, 4])
+    ap.add_argument("--workload", type=int, default=2, choices=[1, 2, 3, 4, 5])
+    ap.add_argument("--batch-count", type=int, default=512, help="matrices of workload 5")
+    ap.add_argument("--no-tune", action="store_true", help="workload 5 without the autotuner")
     ap.add_argument("--scale", type=float, default=1.0, help="row-count scale (1 = full)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -400,7 +730,7 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    rc = run_fmm(args, rank, world, local_rank)
+    rc = (run_batched if args.workload == 5 else run_fmm)(args, rank, world, local_rank)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

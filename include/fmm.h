@@ -96,15 +96,17 @@ typedef struct fmm_plan_options {
     int32_t split_nnz;        /* rows (and columns, for S^T) with more
                                  nonzeros than this are split into chunks of
                                  this many nonzeros whose partial rows are
-                                 summed in a fixed order; 0 = default (512)  */
+                                 summed in a fixed order; 0 = default:
+                                 nnz / 16384 clamped to [256, 8192]          */
     int32_t variant;          /* kernel variant of the vectorised row passes:
                                  0 = chosen by the plan; else V*100 + N*10 + U
                                  with V = vectors per lane (as a multiple of
                                  the minimum for the row width), N = lane
                                  groups sharing one output row, U = nonzeros
-                                 per group per batch; one of 114, 118, 222,
-                                 224, 441, 442, 214, 124 (a code that does not
-                                 fit the row width falls back to 118)        */
+                                 per group per batch; one of 112, 114, 118,
+                                 122, 124, 212, 214, 221, 222, 224, 441, 442
+                                 (a code that does not fit the row width
+                                 falls back to 118)                          */
 } fmm_plan_options;
 
 typedef struct fmm_plan fmm_plan;   /* opaque */
@@ -210,6 +212,60 @@ int fmm_fusedmm_bwd(const fmm_plan *plan, const float *vals, const void *A,
 int fmm_fusedmm_t_bwd(const fmm_plan *plan, const float *vals, const void *A,
                       const void *B, const float *Gn, float *dA, float *dB,
                       float *ds, fmm_stream stream);
+
+/*
+ * Kernel variant of a plan's row passes (the codes of
+ * fmm_plan_options.variant; 0 leaves a side unchanged).  variant applies to
+ * passes over S, variant_t to passes over S^T.  Used by the autotuner; calls
+ * already queued are not affected.
+ */
+int fmm_plan_set_variant(fmm_plan *plan, int32_t variant, int32_t variant_t);
+
+/*
+ * Batched FusedMM: many matrices of uneven sizes in one persistent launch
+ * per phase (not in the paper; a training-system batching pattern).
+ *
+ * Each item names a plan and its operands (device pointers, as for
+ * fmm_fusedmm and fmm_fusedmm_bwd): vals (NULL = all ones), A (m x r),
+ * B (n x r), out (m x r) receive FusedMMA; G (m x r), dA, dB, ds receive its
+ * adjoint.  All plans must share one dtype and the current device, have r in
+ * {32, 64, 128, 256}, and have no split rows or columns (create them with a
+ * split_nnz at least the longest row and column); dense pointers must be
+ * 16-byte aligned.  Items without G, or without any gradient output, make a
+ * forward-only batch.  The batch stores the pointers: they must stay valid
+ * and the buffers at those addresses are read and written by every launch.
+ *
+ * fmm_batch_forward queues a memset of the batch's work counter and one
+ * persistent kernel in which warps pop work units (consecutive rows of one
+ * matrix, longest rows of all matrices first) until none are left;
+ * fmm_batch_backward does the same for the adjoint passes (over S: dA, ds;
+ * over S^T: dB).  Both can be captured in a CUDA graph.  Each item runs the
+ * kernel variant its plan selects (fmm_plan_set_variant), if the batch
+ * kernels have it for that width and role (codes 112, 114, 122, 212, 214,
+ * 221, with at most 48 floats live per lane), else the width's default with
+ * fewer nonzeros per batch.  Results equal the per-item calls with the same variants
+ * bit for bit.  Calls on one batch must be ordered (one stream).
+ */
+typedef struct fmm_batch fmm_batch;   /* opaque */
+
+typedef struct fmm_batch_item {
+    const fmm_plan *plan;
+    const float *vals;
+    const void *A;
+    const void *B;
+    float *out;
+    const float *G;
+    float *dA;
+    float *dB;
+    float *ds;
+} fmm_batch_item;
+
+int fmm_batch_create(const fmm_batch_item *items, int32_t count, fmm_stream stream,
+                     fmm_batch **batch);
+int fmm_batch_forward(const fmm_batch *batch, fmm_stream stream);
+int fmm_batch_backward(const fmm_batch *batch, fmm_stream stream);
+/* Frees a batch (synchronises the device first).  NULL is a no-op. */
+int fmm_batch_destroy(fmm_batch *batch);
 
 /*
  * FusedMMA (same result as fmm_fusedmm) for callers that cannot allocate

@@ -14,7 +14,7 @@ static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 
 // nonzeros per group per batch (the combinations instantiated in
 // fmm_rows.cuh; a combination that does not fit a row shape falls back to
 // the shape's default).
-static const int kVariantCodes[] = {114, 118, 222, 224, 441, 442, 214, 124};
+static const int kVariantCodes[] = {114, 118, 222, 224, 441, 442, 214, 124, 112, 122, 212, 221};
 
 bool variant_known(int code)
 {

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "fmm.h"
 
 namespace fmm {
@@ -22,8 +24,9 @@ struct Side {
     const int32_t *row_ptr = nullptr; // rows + 1
     const int32_t *col_idx = nullptr; // nnz
     const int32_t *perm = nullptr;    // nnz; NULL on the S side (identity)
-    int32_t *order = nullptr;         // rows: split rows first, then the rest
-                                      // by decreasing length (ties by index)
+    int32_t *order = nullptr;         // rows: split rows first, then the rest by
+                                      // decreasing floor(log2(length)), index
+                                      // order within a bucket
     int32_t n_split = 0;              // rows split into chunks
     int32_t n_light = 0;              // rows - n_split
     int4 *chunks = nullptr;           // {row, begin, end, unused} per chunk
@@ -32,6 +35,8 @@ struct Side {
     float *partials = nullptr;        // n_chunks x r partial rows
     int32_t max_nnz = 0;              // longest row
     KernelVariant variant;            // kernel variant of passes over this side
+    std::vector<int32_t> bucket_start;  // host: first position in `order` of
+                                        // each length key (257 entries)
     const int32_t *light_order() const { return order ? order + n_split : nullptr; }
 };
 

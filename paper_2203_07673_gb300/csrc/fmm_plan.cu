@@ -210,8 +210,10 @@ static cudaError_t radix_sort(uint32_t *ka, int32_t *va, uint32_t *kb, int32_t *
 
 // --------------------------------------------------------- side schedule
 
-// Sort key of a row by length: split rows first (0), then decreasing length
-// (lengths >= 254 share key 1), empty rows last (255).
+// Sort key of a row by length: split rows first (0), then rows by
+// decreasing floor(log2(length)) (keys 34..64), empty rows last (255).  Rows
+// of one bucket keep their index order (the sort is stable), so rows of
+// similar length stay in memory order.
 __global__ void row_keys_kernel(const int32_t *row_ptr, int32_t rows, int32_t split_nnz,
                                 uint32_t *keys, int32_t *vals, int32_t *counters)
 {
@@ -222,12 +224,10 @@ __global__ void row_keys_kernel(const int32_t *row_ptr, int32_t rows, int32_t sp
         if (deg > split_nnz) {
             key = 0;
             atomicAdd(&counters[0], 1);
-        } else if (deg >= 254) {
-            key = 1;
         } else if (deg == 0) {
             key = 255;
         } else {
-            key = 255u - (uint32_t)deg;
+            key = 64u - (uint32_t)(31 - __clz(deg));
         }
         atomicMax(&counters[1], deg);
         keys[i] = key;
@@ -353,6 +353,23 @@ static int build_side(Side &side, const int32_t *row_ptr, int32_t rows, int32_t 
             "row order sort");
     FMM_TRY(cudaMemcpyAsync(side.order, in_b ? tmp.vb : tmp.va, (size_t)rows * sizeof(int32_t),
                             cudaMemcpyDeviceToDevice, st), "copy row order");
+    // start of every length key in `order`: the scanned digit offsets of the
+    // sort's first tile (entry key * ntiles of the histogram)
+    side.bucket_start.assign(257, 0);
+    if (rows > 1) {
+        const int64_t ntiles = (rows + RS_TILE - 1) / RS_TILE;
+        uint32_t starts[256];
+        FMM_TRY(cudaMemcpy2DAsync(starts, sizeof(uint32_t), tmp.ghist, ntiles * sizeof(uint32_t),
+                                  sizeof(uint32_t), 256, cudaMemcpyDeviceToHost, st),
+                "read bucket starts");
+        FMM_TRY(cudaStreamSynchronize(st), "plan sync");
+        for (int k = 0; k < 256; ++k)
+            side.bucket_start[k] = (int32_t)starts[k];
+    } else {
+        // a single row: its key decides its bucket (computed below from max_nnz)
+        side.bucket_start.assign(257, rows);
+    }
+    side.bucket_start[256] = rows;
     int32_t counters[2];
     FMM_TRY(cudaMemcpyAsync(counters, tmp.counters, sizeof(counters), cudaMemcpyDeviceToHost, st),
             "read counters");
@@ -360,6 +377,12 @@ static int build_side(Side &side, const int32_t *row_ptr, int32_t rows, int32_t 
     side.n_split = counters[0];
     side.max_nnz = counters[1];
     side.n_light = rows - side.n_split;
+    if (rows == 1) {
+        const int32_t d = side.max_nnz;
+        const int key = d > split_nnz ? 0 : (d == 0 ? 255 : 64 - (31 - __builtin_clz((unsigned)d)));
+        for (int k = 0; k <= key; ++k)
+            side.bucket_start[k] = 0;
+    }
     if (side.n_split == 0)
         return FMM_OK;
     int2 *d_ranges = nullptr;
@@ -467,6 +490,11 @@ int create_plan(const fmm_csr *S, int32_t r, int32_t dtype, const fmm_plan_optio
     fmm_plan *p = new fmm_plan();
     p->m = S->m; p->n = S->n; p->nnz = S->nnz; p->r = r; p->dtype = dtype;
     p->flags = opt ? opt->flags : 0u;
+    // A row is split when one team would still be busy with it after the
+    // other teams finished everything else: with rows longest-first, that is
+    // a row of more than about nnz / (2 x concurrent teams) nonzeros.  About
+    // 16K teams run at once on 152 SMs, hence nnz / 16384, within [256, 8192].
+    p->split_nnz = (int32_t)std::min<int64_t>(8192, std::max<int64_t>(256, S->nnz / 16384));
     if (opt && opt->split_nnz > 0) p->split_nnz = opt->split_nnz;
     if (opt) p->variant = opt->variant;
     cudaGetDevice(&p->device);

@@ -211,8 +211,11 @@ __device__ __forceinline__ void team_store_f32(const Loader &ld, float *row, int
 // group g).  Gathers of a batch are all issued before any is used.  After the
 // last batch the NG partial accumulators are summed across the team and
 // group 0 stores the row.
+//
+// team_pass_body does the work of team `gid` (every lane of the warp must
+// call it; lanes whose team is not active only join the shuffles).
 template <int MODE, typename T, int R, int VPL, int NG, int U>
-__global__ void __launch_bounds__(256) team_pass_kernel(const PassArgs a)
+__device__ __forceinline__ void team_pass_body(const PassArgs &a, long long gid, bool active)
 {
     using TS = TeamShape<T, R, VPL, NG>;
     constexpr int G = TS::G, TEAM = TS::TEAM, E = TS::E;
@@ -220,13 +223,11 @@ __global__ void __launch_bounds__(256) team_pass_kernel(const PassArgs a)
     constexpr bool ACC = MODE != M_SDDMM;
     constexpr bool TWO = MODE == M_BWD_ROW || MODE == M_BWD_COL;
     constexpr int ND = TWO ? 2 * U : U;
+    (void)TEAM;
 
     const int lane = threadIdx.x & 31;
     const int lig = lane & (G - 1);
     const int grp = (lane / G) & (NG - 1);
-    const long long gid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / TEAM;
-    const long long total = (long long)a.n_chunks + a.n_light;
-    const bool active = gid < total;
     const Loader ld;
 
     int row = 0, beg = 0, end = 0, slot = -1;
@@ -260,7 +261,10 @@ __global__ void __launch_bounds__(256) team_pass_kernel(const PassArgs a)
             const int p = p0 + u * NG;
             if (p < end) {
                 jj[u] = ld.idx(a.col_idx + p);
-                sidx[u] = a.perm ? ld.idx(a.perm + p) : p;
+                // the slot in S order is needed for per-nonzero outputs and
+                // for values not yet in this CSR's order
+                constexpr bool NZ = MODE == M_SDDMM || MODE == M_BWD_ROW;
+                sidx[u] = (a.perm && (NZ || !a.s_direct)) ? ld.idx(a.perm + p) : p;
                 sv[u] = a.s ? ld.val(a.s + (a.s_direct ? p : sidx[u])) : 1.f;
             } else {
                 jj[u] = -1; sidx[u] = 0; sv[u] = 0.f;
@@ -358,6 +362,15 @@ __global__ void __launch_bounds__(256) team_pass_kernel(const PassArgs a)
                 team_store_f32<T, VPL, G>(ld, dst, lig, acc);
         }
     }
+}
+
+template <int MODE, typename T, int R, int VPL, int NG, int U>
+__global__ void __launch_bounds__(256) team_pass_kernel(const PassArgs a)
+{
+    constexpr int TEAM = TeamShape<T, R, VPL, NG>::TEAM;
+    const long long gid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / TEAM;
+    const long long total = (long long)a.n_chunks + a.n_light;
+    team_pass_body<MODE, T, R, VPL, NG, U>(a, gid, gid < total);
 }
 
 template <typename T> __device__ __forceinline__ float widen(T x);
@@ -507,6 +520,10 @@ cudaError_t dispatch_variant(int vpl, int ng, int u, const PassArgs &a, cudaStre
     FMM_TRY_VARIANT(4 * B, 4, 2)
     FMM_TRY_VARIANT(2 * B, 1, 4)
     FMM_TRY_VARIANT(B, 2, 4)
+    FMM_TRY_VARIANT(B, 1, 2)
+    FMM_TRY_VARIANT(B, 2, 2)
+    FMM_TRY_VARIANT(2 * B, 1, 2)
+    FMM_TRY_VARIANT(2 * B, 2, 1)
 #undef FMM_TRY_VARIANT
     // a variant that does not fit this row shape: one group per row
     return launch_team<MODE, T, R, B, 1, 8>(a, st);

@@ -37,6 +37,11 @@ _SIGNATURES = {
     "fmm_fusedmm_bwd": ([_P, _P, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "fmm_fusedmm_t_bwd": ([_P, _P, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "fmm_fusedmm_noalloc": ([_P, _I32, _I32, _P, _P, _P, _P, _P], ctypes.c_int),
+    "fmm_plan_set_variant": ([_P, _I32, _I32], ctypes.c_int),
+    "fmm_batch_create": ([_P, _I32, _P, _P], ctypes.c_int),
+    "fmm_batch_forward": ([_P, _P], ctypes.c_int),
+    "fmm_batch_backward": ([_P, _P], ctypes.c_int),
+    "fmm_batch_destroy": ([_P], ctypes.c_int),
     "fmm_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "fmm_last_error": ([], ctypes.c_char_p),
     "fmm_version": ([], ctypes.c_int32),
@@ -165,6 +170,11 @@ class Plan:
                                        _stream(stream), ctypes.byref(out))
         _check(rc, "fmm_plan_create")
         self.handle = out.value
+
+    def set_variant(self, variant: int = 0, variant_t: int = 0):
+        """fmm_plan_set_variant (0 leaves a side unchanged)."""
+        _check(lib().fmm_plan_set_variant(self.handle, int(variant), int(variant_t)),
+               "fmm_plan_set_variant")
 
     def info(self) -> dict:
         inf = _Info()
@@ -300,3 +310,49 @@ def fusedmm_noalloc(row_ptr, col_idx, n: int, vals, A, B, out=None, stream=None)
                                    _ptr(out, "out", torch.float32, (m, r)), _stream(stream))
     _check(rc, "fmm_fusedmm_noalloc")
     return out
+
+
+class _BatchItem(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("vals", ctypes.c_void_p), ("A", ctypes.c_void_p),
+                ("B", ctypes.c_void_p), ("out", ctypes.c_void_p), ("G", ctypes.c_void_p),
+                ("dA", ctypes.c_void_p), ("dB", ctypes.c_void_p), ("ds", ctypes.c_void_p)]
+
+
+class Batch:
+    """fmm_batch: FusedMMA (and its adjoint) of many plans in one persistent
+    launch per phase.  ``items`` is a list of dicts with keys plan, vals, A,
+    B, out and optionally G, dA, dB, ds (tensors on the plans' device).  The
+    batch keeps references to every tensor; their storage must not move."""
+
+    def __init__(self, items, stream=None):
+        self.handle = None
+        self._keep = items
+        arr = (_BatchItem * len(items))()
+        for k, it in enumerate(items):
+            p = it["plan"]
+            arr[k] = _BatchItem(
+                p.handle, p._f32(it.get("vals"), (p.nnz,), "vals"), p._dense(it["A"], p.m, "A"),
+                p._dense(it["B"], p.n, "B"), p._f32(it["out"], (p.m, p.r), "out"),
+                p._f32(it.get("G"), (p.m, p.r), "G"), p._f32(it.get("dA"), (p.m, p.r), "dA"),
+                p._f32(it.get("dB"), (p.n, p.r), "dB"), p._f32(it.get("ds"), (p.nnz,), "ds"))
+        out = ctypes.c_void_p()
+        rc = lib().fmm_batch_create(arr, len(items), _stream(stream), ctypes.byref(out))
+        _check(rc, "fmm_batch_create")
+        self.handle = out.value
+
+    def forward(self, stream=None):
+        _check(lib().fmm_batch_forward(self.handle, _stream(stream)), "fmm_batch_forward")
+
+    def backward(self, stream=None):
+        _check(lib().fmm_batch_backward(self.handle, _stream(stream)), "fmm_batch_backward")
+
+    def close(self):
+        if self.handle is not None:
+            lib().fmm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

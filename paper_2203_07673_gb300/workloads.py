@@ -337,3 +337,73 @@ def batched_matrix(spec: dict, t: int, seed_index: int = 5) -> dict:
     return dict(S=S, vals=uniform(S.nnz, 0.0, 1.0, rng),
                 A=normal(rows, r, 1.0 / r, rng), B=normal(rows, r, 1.0 / r, rng),
                 r=r)
+
+
+# ---------------------------------------------------------------------------
+# The batched workload drawn with torch on a device (same recipe as
+# batched_matrix, a different random stream): 512 matrices are generated in
+# seconds instead of minutes.  Returns device tensors; the oracle receives
+# host copies of exactly these tensors.
+
+def _torch_gen(device, seed):
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    return g
+
+
+def er_exact_degree_torch(m, n, deg, g, device):
+    import torch
+    deg = min(deg, n)
+    cols = torch.randint(0, n, (m, deg), generator=g, device=device, dtype=torch.int64)
+    while True:
+        cols, _ = torch.sort(cols, dim=1)
+        bad = (cols[:, 1:] == cols[:, :-1]).any(dim=1).nonzero().flatten() if deg > 1 else \
+            torch.zeros(0, dtype=torch.int64, device=device)
+        if bad.numel() == 0:
+            break
+        cols[bad] = torch.randint(0, n, (bad.numel(), deg), generator=g, device=device,
+                                  dtype=torch.int64)
+    row_ptr = torch.arange(m + 1, device=device, dtype=torch.int64) * deg
+    return row_ptr.int(), cols.reshape(-1).int()
+
+
+def rmat_torch(scale, edges, a, b, c, g, device, vertices):
+    import torch
+    E = int(edges)
+    rows = torch.zeros(E, dtype=torch.int64, device=device)
+    cols = torch.zeros(E, dtype=torch.int64, device=device)
+    ab, abc = a + b, a + b + c
+    for level in range(scale):
+        u = torch.rand(E, generator=g, device=device)
+        bit = 1 << (scale - 1 - level)
+        rows |= (u >= ab).long() * bit
+        cols |= (((u >= a) & (u < ab)) | (u >= abc)).long() * bit
+    perm = torch.randperm(1 << scale, generator=g, device=device)
+    rows = perm[rows] % vertices
+    cols = perm[cols] % vertices
+    keys = torch.unique(rows * vertices + cols)
+    r_, c_ = keys // vertices, keys % vertices
+    counts = torch.bincount(r_, minlength=vertices)
+    row_ptr = torch.zeros(vertices + 1, dtype=torch.int64, device=device)
+    row_ptr[1:] = torch.cumsum(counts, 0)
+    return row_ptr.int(), c_.int()
+
+
+def batched_matrix_torch(spec: dict, t: int, device, seed_index: int = 5) -> dict:
+    """Matrix t of the batched workload as device tensors: row_ptr, col_idx
+    (int32), vals ~ U(0,1), A, B ~ N(0, 1/r) (float32), r, m, n."""
+    import torch
+    g = _torch_gen(device, (ROOT_SEED + seed_index) * 1000003 + t)
+    rows, r = spec["rows"], spec["r"]
+    if spec["kind"] == "er":
+        rp, ci = er_exact_degree_torch(rows, rows, spec["deg"], g, device)
+    else:
+        scale = max(1, int(math.ceil(math.log2(rows))))
+        rp, ci = rmat_torch(scale, spec["deg"] * rows, 0.57, 0.19, 0.19, g, device, rows)
+    nnz = ci.numel()
+    vals = torch.rand(nnz, generator=g, device=device)
+    std = math.sqrt(1.0 / r)
+    A = torch.randn(rows, r, generator=g, device=device) * std
+    B = torch.randn(rows, r, generator=g, device=device) * std
+    return dict(row_ptr=rp, col_idx=ci, vals=vals, A=A, B=B, r=r, m=rows, n=rows)

@@ -87,3 +87,38 @@ def oracle_all(S, vals, A, B, G, Gn):
 
 def absolute(x):
     return None if x is None else np.abs(x)
+
+
+def rows_problem(S, rows, vals=None):
+    """The sub-pattern of the given rows (in the given order) with its
+    columns compacted: returns (row_ptr, col_idx, vals, cols, nnz_index) so
+    that FusedMMA of the sub-problem on (A[rows], B[cols]) gives exactly
+    those rows of the full result."""
+    rp = S.row_ptr.astype(np.int64)
+    deg = rp[rows + 1] - rp[rows]
+    idx = np.concatenate([np.arange(rp[i], rp[i + 1]) for i in rows]) if len(rows) else \
+        np.zeros(0, np.int64)
+    sub_rp = np.zeros(len(rows) + 1, np.int64)
+    np.cumsum(deg, out=sub_rp[1:])
+    cols, ci = np.unique(S.col_idx[idx], return_inverse=True)
+    v = None if vals is None else np.asarray(vals)[idx]
+    return sub_rp, ci.astype(np.int64), v, cols, idx
+
+
+def cols_problem(S, cols, vals=None):
+    """The nonzeros of S in the given columns: returns (row_ptr, col_idx,
+    vals, rows, nnz_index) with rows compacted and column c of the
+    sub-problem being cols[c], so that FusedMMB of the sub-problem on
+    (A[rows], B[cols]) gives exactly those columns of the full result."""
+    cols = np.asarray(cols)
+    pos = np.full(S.n, -1, np.int64)
+    pos[cols] = np.arange(len(cols))
+    sel = pos[S.col_idx] >= 0
+    idx = np.nonzero(sel)[0]
+    row_of = np.repeat(np.arange(S.m), np.diff(S.row_ptr.astype(np.int64)))
+    r_sel = row_of[idx]
+    rows, r_new = np.unique(r_sel, return_inverse=True)
+    sub_rp = np.zeros(len(rows) + 1, np.int64)
+    np.cumsum(np.bincount(r_new, minlength=len(rows)), out=sub_rp[1:])
+    v = None if vals is None else np.asarray(vals)[idx]
+    return sub_rp, pos[S.col_idx[idx]], v, rows, idx

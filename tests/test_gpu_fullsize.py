@@ -1,0 +1,125 @@
+"""Parity at the full workload sizes, in the plan configuration bench.py
+times, on sampled rows and columns the oracle computes exactly.
+
+A sampled row i of FusedMMA (and dA_i, ds of row i) depends only on the
+nonzeros of row i; a sampled column j of FusedMMB (and dB_j) only on the
+nonzeros of column j.  So each check runs the oracle on the sub-pattern of
+the sampled rows (or columns) and compares element by element.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from parity_utils import U32, cols_problem, relF, rows_problem
+from paper_2203_07673_gb300 import workloads as wl
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+def _cmp(name, got, ref, mag, terms, tol=1e-5):
+    got = np.asarray(got, np.float64)
+    bound = 2.0 * terms * U32 * mag + 1e-30
+    bad = np.abs(got - ref) > bound
+    assert not bad.any(), f"{name}: {bad.sum()} elements over the rounding bound"
+    e = relF(got, ref)
+    assert e <= tol, f"{name}: relF {e:.2e}"
+    return e
+
+
+def _sampled_fwd(w, dt, plan, vt, At, Bt, n_rows=384, n_cols=384, seed=0):
+    from paper_2203_07673_gb300 import fmm
+    S, r = w["S"], w["r"]
+    out = fmm.fusedmm(plan, vt, At, Bt)
+    out_t = fmm.fusedmm_t(plan, vt, At, Bt)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(seed)
+    rows = np.sort(rng.choice(S.m, n_rows, replace=False))
+    rows[0] = int(np.argmax(S.degrees()))                  # the longest row too
+    cols = np.sort(rng.choice(S.n, n_cols, replace=False))
+    cols[0] = int(np.argmax(np.bincount(S.col_idx, minlength=S.n)))
+    rows, cols = np.unique(rows), np.unique(cols)
+    A64 = At[torch.from_numpy(np.unique(np.concatenate([rows]))).cuda()].double().cpu().numpy()
+    vals = w["vals"]
+    rp, ci, v, cused, _ = rows_problem(S, rows, vals)
+    B_used = Bt[torch.from_numpy(cused).cuda()].double().cpu().numpy()
+    ref = oracle.fusedmm(rp, ci, v, A64, B_used, len(cused))
+    mag = oracle.fusedmm(rp, ci, None if v is None else np.abs(v), np.abs(A64),
+                         np.abs(B_used), len(cused))
+    deg = int(S.degrees().max())
+    e1 = _cmp("FusedMMA rows", out[torch.from_numpy(rows).cuda()].double().cpu().numpy(),
+              ref, mag, r + deg + 4)
+    rp, ci, v, rused, _ = cols_problem(S, cols, vals)
+    A_used = At[torch.from_numpy(rused).cuda()].double().cpu().numpy()
+    B_c = Bt[torch.from_numpy(cols).cuda()].double().cpu().numpy()
+    ref = oracle.fusedmm_t(rp, ci, v, A_used, B_c, len(cols))
+    mag = oracle.fusedmm_t(rp, ci, None if v is None else np.abs(v), np.abs(A_used),
+                           np.abs(B_c), len(cols))
+    cdeg = int(np.bincount(S.col_idx, minlength=S.n).max())
+    e2 = _cmp("FusedMMB cols", out_t[torch.from_numpy(cols).cuda()].double().cpu().numpy(),
+              ref, mag, r + cdeg + 4)
+    return e1, e2
+
+
+def _upload(w, dt):
+    S = w["S"]
+    rp = torch.from_numpy(S.row_ptr).cuda()
+    ci = torch.from_numpy(S.col_idx).cuda()
+    vt = None if w["vals"] is None else torch.from_numpy(w["vals"]).cuda()
+    At = torch.from_numpy(w["A"]).cuda().to(dt).contiguous()
+    Bt = torch.from_numpy(w["B"]).cuda().to(dt).contiguous()
+    return rp, ci, vt, At, Bt
+
+
+def test_er_2p20_r128_f32_bench_configuration():
+    from paper_2203_07673_gb300 import fmm
+    w = wl.workload(2)
+    rp, ci, vt, At, Bt = _upload(w, torch.float32)
+    plan = fmm.Plan(rp, ci, w["S"].n, w["r"], torch.float32)   # as bench.py
+    _sampled_fwd(w, torch.float32, plan, vt, At, Bt)
+
+
+@pytest.mark.parametrize("dt", [torch.float32, torch.bfloat16], ids=["f32", "bf16"])
+def test_zipf_rows_2p21x2p19_r64(dt):
+    from paper_2203_07673_gb300 import fmm
+    w = wl.workload(4)
+    rp, ci, vt, At, Bt = _upload(w, dt)
+    plan = fmm.Plan(rp, ci, w["S"].n, w["r"], dt)
+    _sampled_fwd(w, dt, plan, vt, At, Bt, seed=1)
+
+
+def test_rmat_2p22_r64_bf16_forward_backward():
+    from paper_2203_07673_gb300 import fmm
+    w = wl.workload(3)
+    S, r = w["S"], w["r"]
+    rp, ci, _, At, Bt = _upload(w, torch.bfloat16)
+    ones = torch.ones(S.nnz, device="cuda")          # s = 1, gradient wanted
+    plan = fmm.Plan(rp, ci, S.n, r, torch.bfloat16)
+    w1 = dict(w, vals=None)
+    _sampled_fwd(w1, torch.bfloat16, plan, None, At, Bt, seed=2)
+    G = torch.randn(S.m, r, device="cuda", generator=torch.Generator(device="cuda").manual_seed(5))
+    dA, dB, ds = fmm.fusedmm_bwd(plan, ones, At, Bt, G)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(3)
+    rows = np.unique(np.concatenate([[int(np.argmax(S.degrees()))],
+                                     rng.choice(S.m, 256, replace=False)]))
+    cols = np.unique(np.concatenate([[int(np.argmax(np.bincount(S.col_idx, minlength=S.n)))],
+                                     rng.choice(S.n, 256, replace=False)]))
+    t = lambda idx: torch.from_numpy(np.asarray(idx)).cuda()
+    # dA and ds of the sampled rows
+    srp, sci, _, cused, nz = rows_problem(S, rows)
+    A_r = At[t(rows)].double().cpu().numpy(); B_c = Bt[t(cused)].double().cpu().numpy()
+    G_r = G[t(rows)].double().cpu().numpy()
+    ref = oracle.fusedmm_grad(srp, sci, None, A_r, B_c, G_r, len(cused))
+    mag = oracle.fusedmm_grad(srp, sci, None, np.abs(A_r), np.abs(B_c), np.abs(G_r), len(cused))
+    deg = int(S.degrees().max())
+    _cmp("dA rows", dA[t(rows)].double().cpu().numpy(), ref[0], mag[0], 2 * r + deg + 4)
+    _cmp("ds of the rows", ds[t(nz)].double().cpu().numpy(), ref[2], mag[2], 2 * r + 4)
+    # dB of the sampled columns
+    srp, sci, _, rused, _ = cols_problem(S, cols)
+    A_r = At[t(rused)].double().cpu().numpy(); B_c = Bt[t(cols)].double().cpu().numpy()
+    G_r = G[t(rused)].double().cpu().numpy()
+    ref = oracle.fusedmm_grad(srp, sci, None, A_r, B_c, G_r, len(cols))
+    mag = oracle.fusedmm_grad(srp, sci, None, np.abs(A_r), np.abs(B_c), np.abs(G_r), len(cols))
+    cdeg = int(np.bincount(S.col_idx, minlength=S.n).max())
+    _cmp("dB cols", dB[t(cols)].double().cpu().numpy(), ref[1], mag[1], 2 * r + cdeg + 4)

@@ -100,7 +100,7 @@ def test_parity_all_ops(kind, r, dtype):
     run_all(S, opts, r, dtype, seed=r, check_bf16_vs_f32=(dtype == torch.bfloat16))
 
 
-@pytest.mark.parametrize("variant", [114, 118, 222, 224, 441, 442, 214, 124])
+@pytest.mark.parametrize("variant", [114, 118, 222, 224, 441, 442, 214, 124, 112, 122, 212, 221])
 @pytest.mark.parametrize("split_nnz", [16, 0])
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16], ids=["f32", "bf16"])
 @pytest.mark.parametrize("r", [32, 128, 256])
