@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 METRIC = ("FusedMM nnz·r/s and HBM GB/s vs peak; fused vs unfused SDDMM→SpMM, "
           "same GPU")
 UNIT = "nnz*r/s"
-PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "roofline_traffic.txt")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2203_07673_gb300", "csrc", f)
                   for f in ("fmm_rows.cuh", "fmm_rows_f32.cu", "fmm_rows_bf16.cu",
                             "fmm_internal.cuh")]
@@ -47,6 +47,25 @@ def kernel_source_sha() -> str:
         with open(f, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
+
+
+def read_traffic(workload, call, dtype):
+    """DRAM bytes per call from profiles/roofline_traffic.txt, if captured on
+    the current kernel sources; else (None, reason)."""
+    try:
+        sha = kernel_source_sha()
+        with open(PROFILE_TRAFFIC) as fh:
+            for line in fh:
+                if line.startswith("#") or "|" not in line:
+                    continue
+                f = [x.strip() for x in line.split("|")]
+                if f[0] == workload and f[1] == call and f[2] == dtype:
+                    if f[4] != sha:
+                        return None, "ncu capture predates the current kernel source"
+                    return float(f[3]), f[5]
+    except OSError:
+        pass
+    return None, "no ncu capture for this workload and call"
 
 
 def gather_model_bytes(m, nnz, r, e, vals=True):
@@ -447,16 +466,7 @@ def run_fmm(args, rank, world, local_rank):
     dom = int(np.argmax(call_ms))
     dom_name, dom_bytes = calls[dom]
     achieved = dom_bytes / (call_ms[dom] / 1e3) / 1e9
-    traffic, traffic_note = None, "no ncu capture for the current kernel source"
-    try:
-        with open(PROFILE_TRAFFIC) as fh:
-            prof = json.load(fh)
-        entry = prof.get(f"{w['name']}|{dom_name}|{w['dtype']}")
-        if entry and entry.get("source_sha1") == kernel_source_sha():
-            traffic = float(entry["dram_bytes_per_call"])
-            traffic_note = entry.get("note", "")
-    except Exception:
-        pass
+    traffic, traffic_note = read_traffic(w["name"], dom_name, w["dtype"])
     launches = {"fmm_fusedmm": 1 + (1 if info["split_rows"] else 0),
                 "fmm_fusedmm_t": 1 + (1 if info["split_cols"] else 0) + (1 if vals is not None else 0),
                 "fmm_fusedmm_bwd": 3 + (1 if info["split_rows"] else 0) + (1 if info["split_cols"] else 0)}
