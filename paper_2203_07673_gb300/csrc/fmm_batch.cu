@@ -177,8 +177,8 @@ int teams_per_warp(int dtype, int r, int code)
 }
 
 // Units of one pass: consecutive teams within one length bucket, about 512
-// nonzeros of work each (rows of bucket key k have 2^(64-k) to 2^(65-k) - 1
-// nonzeros), a multiple of the warp's team count.
+// nonzeros of work each (from the bucket's shortest row length), a multiple
+// of the warp's team count.
 void make_units(std::vector<std::pair<int, int4>> &out, const Side &side, int item, int kind,
                 int tpw)
 {
@@ -187,8 +187,8 @@ void make_units(std::vector<std::pair<int, int4>> &out, const Side &side, int it
         if (b1 <= b0)
             continue;
         int per = tpw;
-        if (key >= 34 && key < 255) {
-            const int lo = 1 << (64 - key);   // shortest row of the bucket
+        if (key >= 136 && key < 255) {
+            const int lo = length_key_min((uint32_t)key);
             per = std::max(tpw, std::min(256, 512 / std::max(lo, 1)));
             per = (per + tpw - 1) / tpw * tpw;
         } else if (key == 255) {

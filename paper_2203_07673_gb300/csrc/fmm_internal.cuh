@@ -24,9 +24,9 @@ struct Side {
     const int32_t *row_ptr = nullptr; // rows + 1
     const int32_t *col_idx = nullptr; // nnz
     const int32_t *perm = nullptr;    // nnz; NULL on the S side (identity)
-    int32_t *order = nullptr;         // rows: split rows first, then the rest by
-                                      // decreasing floor(log2(length)), index
-                                      // order within a bucket
+    int32_t *order = nullptr;         // rows: split rows first, then the rest in
+                                      // length buckets (length_key), index order
+                                      // within a bucket
     int32_t n_split = 0;              // rows split into chunks
     int32_t n_light = 0;              // rows - n_split
     int4 *chunks = nullptr;           // {row, begin, end, unused} per chunk
@@ -39,6 +39,32 @@ struct Side {
                                         // each length key (257 entries)
     const int32_t *light_order() const { return order ? order + n_split : nullptr; }
 };
+
+// Length key of a row for the plan's row order (ascending key = longer rows
+// first): 0 for split rows, 255 for empty rows, else 254 - q(d) with q(d) =
+// d - 1 for d < 4 and 3 + 4 (k - 2) + the two bits after the leading one for
+// 2^k <= d < 2^(k+1): four buckets per power of two, so rows of one bucket
+// differ in length by less than a quarter.
+__host__ __device__ inline uint32_t length_key(int32_t d, int32_t split_nnz)
+{
+    if (d > split_nnz) return 0u;
+    if (d <= 0) return 255u;
+    if (d < 4) return 254u - (uint32_t)(d - 1);
+    int k = 31;
+    while (!((uint32_t)d >> k)) --k;
+    const uint32_t sub = ((uint32_t)d >> (k - 2)) & 3u;
+    return 254u - (3u + 4u * (uint32_t)(k - 2) + sub);
+}
+
+// Shortest row length of a length key in [136, 254].
+inline int32_t length_key_min(uint32_t key)
+{
+    const uint32_t q = 254u - key;
+    if (q < 3) return (int32_t)q + 1;
+    const int k = (int)((q - 3) / 4) + 2;
+    const int sub = (int)((q - 3) % 4);
+    return (1 << k) + sub * (1 << (k - 2));
+}
 
 // Kernel roles.  "local" rows belong to the row being produced; "gathered"
 // rows are fetched per nonzero through col_idx.

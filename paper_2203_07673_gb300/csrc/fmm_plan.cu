@@ -210,25 +210,17 @@ static cudaError_t radix_sort(uint32_t *ka, int32_t *va, uint32_t *kb, int32_t *
 
 // --------------------------------------------------------- side schedule
 
-// Sort key of a row by length: split rows first (0), then rows by
-// decreasing floor(log2(length)) (keys 34..64), empty rows last (255).  Rows
-// of one bucket keep their index order (the sort is stable), so rows of
-// similar length stay in memory order.
+// Sort key of every row (length_key) and the counts of split rows and the
+// longest row.
 __global__ void row_keys_kernel(const int32_t *row_ptr, int32_t rows, int32_t split_nnz,
                                 uint32_t *keys, int32_t *vals, int32_t *counters)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < rows; i += stride) {
         const int32_t deg = row_ptr[i + 1] - row_ptr[i];
-        uint32_t key;
-        if (deg > split_nnz) {
-            key = 0;
+        const uint32_t key = length_key(deg, split_nnz);
+        if (key == 0)
             atomicAdd(&counters[0], 1);
-        } else if (deg == 0) {
-            key = 255;
-        } else {
-            key = 64u - (uint32_t)(31 - __clz(deg));
-        }
         atomicMax(&counters[1], deg);
         keys[i] = key;
         vals[i] = (int32_t)i;
@@ -378,8 +370,7 @@ static int build_side(Side &side, const int32_t *row_ptr, int32_t rows, int32_t 
     side.max_nnz = counters[1];
     side.n_light = rows - side.n_split;
     if (rows == 1) {
-        const int32_t d = side.max_nnz;
-        const int key = d > split_nnz ? 0 : (d == 0 ? 255 : 64 - (31 - __builtin_clz((unsigned)d)));
+        const int key = (int)length_key(side.max_nnz, split_nnz);
         for (int k = 0; k <= key; ++k)
             side.bucket_start[k] = 0;
     }
@@ -571,14 +562,16 @@ int create_plan(const fmm_csr *S, int32_t r, int32_t dtype, const fmm_plan_optio
 }
 
 // Measured on GB300 over ER (32 per row), R-MAT and Zipf-row patterns at
-// r = 64 and 128: one group per output row, 8 elements (32 bytes) per lane
-// and 4 nonzeros per batch is the best or within a few percent of it.
+// r = 64 and 128, FP32 and BF16, forward and both backward passes: one group
+// per output row, 8 elements (32 bytes) per lane and 2 nonzeros per batch is
+// the best or within a few percent of it (the lighter register footprint
+// keeps more rows in flight than deeper batches do).
 KernelVariant default_variant(int32_t r, int32_t dtype, double avg_nnz)
 {
     (void)avg_nnz;
     KernelVariant v;
     v.ng = 1;
-    v.u = 4;
+    v.u = 2;
     const int vecs = r * (dtype == FMM_BF16 ? 2 : 4) / 16;
     // float32 rows of at most 32 vectors hold 4 elements per vector: two
     // vectors per lane make 8 elements

@@ -242,10 +242,11 @@ __device__ __forceinline__ void team_pass_body(const PassArgs &a, long long gid,
     for (int e = 0; e < E; ++e) { lrow[e] = 0.f; acc[e] = 0.f; }
 #pragma unroll
     for (int e = 0; e < (TWO ? E : 1); ++e) hrow[e] = 0.f;
-    if (HAS_L && active)
+    // rows without nonzeros only write zeros: their local rows are not read
+    if (HAS_L && active && end > beg)
         team_load<T, VPL, G>(ld, L + (size_t)row * R, lig, lrow, false);
     if constexpr (MODE == M_BWD_ROW)
-        if (active)
+        if (active && end > beg)
             team_load_f32<T, VPL, G>(ld, a.H + (size_t)row * R, lig, hrow, false);
 
     constexpr int PER = NG * U;
