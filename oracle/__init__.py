@@ -17,6 +17,7 @@ Functions (all return float64 numpy arrays):
   fusedmm_t(rowptr, colidx, vals, A, B, n)    -> out[n, r]     Sec. II (FusedMMB)
   fusedmm_grad(rowptr, colidx, vals, A, B, G, n)     -> (dA, dB, ds)
   fusedmm_t_grad(rowptr, colidx, vals, A, B, Gn, n)  -> (dA, dB, ds)
+  als_cg(rowptr, colidx, c, A, B, lam, iters, side)  -> updated A (side 0) or B (side 1)
 ``vals=None`` means every value of S is 1.
 """
 from __future__ import annotations
@@ -69,6 +70,8 @@ def _load():
                                     ptr, ptr, ptr, ptr],
             "oracle_fusedmm_t_grad": [i64, i64, i64, ptr, ptr, ptr, ptr, ptr,
                                       ptr, ptr, ptr, ptr],
+            "oracle_als_cg": [i64, i64, i64, ptr, ptr, ptr, ptr, ptr, ctypes.c_double,
+                              i64, ctypes.c_int],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -184,3 +187,18 @@ def fusedmm_t_grad(rowptr, colidx, vals, A, B, Gn, n):
     _run(_load().oracle_fusedmm_t_grad, m, n, r, _p(rowptr), _p(colidx),
          _p(vals), _p(A), _p(B), _p(Gn), _p(dA), _p(dB), _p(ds))
     return dA, dB, ds
+
+
+def als_cg(rowptr, colidx, c, A, B, lam, iters, side):
+    """`iters` CG iterations per row of the ALS normal equations (Sec. VI-E),
+    started from the current rows; returns the updated copy of A (side 0) or
+    B (side 1)."""
+    rowptr, colidx, m = _prep(rowptr, colidx, A)
+    A = _dims(A, m).copy()
+    B = _f64(B).copy()
+    n = B.shape[0]
+    c = _f64(c)
+    r = A.shape[1]
+    _run(_load().oracle_als_cg, m, n, r, _p(rowptr), _p(colidx), _p(c), _p(A), _p(B),
+         float(lam), int(iters), int(side))
+    return A if side == 0 else B

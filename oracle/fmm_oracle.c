@@ -28,6 +28,8 @@
  *                           FusedMMB = SpMMB(SDDMM(A,B,S), A)
  *   Sec. IV-A               per-nonzero SpMMA update A_i += S_ij B_j
  *   Sec. IV-B               row form FusedMMA_i = sum_j S_ij <A_i, B_j> B_j
+ *   Sec. VI-E               ALS: per-row least squares M x = b solved by CG,
+ *                           the queries M x batched as FusedMM
  * The gradients are not in the paper; they are the derivatives of the
  * scalar L = <G, FusedMM(S, A, B)> with respect to A, B and the values of S,
  * on a fixed pattern.
@@ -38,6 +40,7 @@
  * an OpenMP parallel-for; the scatter routines run sequentially.
  */
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 
 static double oracle_s(const double *vals, int64_t p)
@@ -245,5 +248,113 @@ int oracle_fusedmm_t_grad(int64_t m, int64_t n, int64_t r,
                     dA[i * r + k] += s * (d * g[k] + w * b[k]);
         }
     }
+    return 0;
+}
+
+/* ---------------------------------------------------------------------------
+ * ALS with conjugate gradients (Sec. VI-E, collaborative filtering).
+ *
+ * The loss is the squared Frobenius norm of (C - SDDMM(A, B, S)) over the
+ * nonzeros of S, plus lambda (|A|^2 + |B|^2).  With B fixed, each row A_i
+ * solves the normal equations M_i x = b_i,
+ *     M_i x = sum_{j in row i} <x, B_j> B_j + lambda x,   b_i = sum_j c_ij B_j,
+ * and with A fixed each row B_j solves the same with the roles exchanged
+ * (the sum running over the nonzeros of column j).  M_i x for all rows at
+ * once is FusedMMA of the 0/1 pattern (FusedMMB for the B side), as the
+ * paper batches the CG queries.  This routine runs `iters` plain CG
+ * iterations per row, started from the current rows, in FP64:
+ *     r = b - M x;  p = r;  rs = <r, r>
+ *     repeat: q = M p;  alpha = rs / <p, q>;  x += alpha p;  r -= alpha q;
+ *             rs' = <r, r>;  p = r + (rs' / rs) p;  rs = rs'
+ * with alpha = 0 when <p, q> <= 0 and the ratio 0 when rs = 0.
+ * side 0 updates A (m x r, in place); side 1 updates B (n x r, in place).
+ * c: nnz values in CSR order.  Sequential.
+ * ------------------------------------------------------------------------ */
+static void oracle_apply_m(int64_t r, double lambda, int64_t deg, const int64_t *nbr,
+                           const double *Y, const double *x, double *out)
+{
+    for (int64_t k = 0; k < r; ++k)
+        out[k] = lambda * x[k];
+    for (int64_t t = 0; t < deg; ++t) {
+        const double *y = Y + nbr[t] * r;
+        double d = oracle_dot(x, y, r);
+        for (int64_t k = 0; k < r; ++k)
+            out[k] += d * y[k];
+    }
+}
+
+int oracle_als_cg(int64_t m, int64_t n, int64_t r, const int64_t *rowptr,
+                  const int64_t *colidx, const double *c, double *A, double *B,
+                  double lambda, int64_t iters, int side)
+{
+    if (oracle_check(m, n, rowptr, colidx))
+        return -1;
+    int64_t nnz = rowptr[m];
+    /* neighbour lists of every row of the side being updated */
+    int64_t rows = side == 0 ? m : n;
+    int64_t *start = calloc((size_t)rows + 1, sizeof(int64_t));
+    int64_t *nbr = malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(int64_t));
+    double *cv = malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(double));
+    double *w = malloc((size_t)(4 * r > 0 ? 4 * r : 1) * sizeof(double));
+    if (!start || !nbr || !cv || !w) {
+        free(start); free(nbr); free(cv); free(w);
+        return -2;
+    }
+    if (side == 0) {
+        for (int64_t i = 0; i <= m; ++i)
+            start[i] = rowptr[i];
+        for (int64_t p = 0; p < nnz; ++p) {
+            nbr[p] = colidx[p];
+            cv[p] = c[p];
+        }
+    } else {
+        for (int64_t p = 0; p < nnz; ++p)
+            start[colidx[p] + 1]++;
+        for (int64_t j = 0; j < n; ++j)
+            start[j + 1] += start[j];
+        int64_t *fill = calloc((size_t)n, sizeof(int64_t));
+        for (int64_t i = 0; i < m; ++i)
+            for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+                int64_t j = colidx[p];
+                int64_t q = start[j] + fill[j]++;
+                nbr[q] = i;
+                cv[q] = c[p];
+            }
+        free(fill);
+    }
+    double *X = side == 0 ? A : B;
+    const double *Y = side == 0 ? B : A;
+    double *res = w, *pp = w + r, *q = w + 2 * r, *bb = w + 3 * r;
+    for (int64_t i = 0; i < rows; ++i) {
+        int64_t deg = start[i + 1] - start[i];
+        const int64_t *nb = nbr + start[i];
+        double *x = X + i * r;
+        for (int64_t k = 0; k < r; ++k)
+            bb[k] = 0.0;
+        for (int64_t t = 0; t < deg; ++t)
+            for (int64_t k = 0; k < r; ++k)
+                bb[k] += cv[start[i] + t] * Y[nb[t] * r + k];
+        oracle_apply_m(r, lambda, deg, nb, Y, x, q);
+        for (int64_t k = 0; k < r; ++k) {
+            res[k] = bb[k] - q[k];
+            pp[k] = res[k];
+        }
+        double rs = oracle_dot(res, res, r);
+        for (int64_t it = 0; it < iters; ++it) {
+            oracle_apply_m(r, lambda, deg, nb, Y, pp, q);
+            double pq = oracle_dot(pp, q, r);
+            double alpha = pq > 0.0 ? rs / pq : 0.0;
+            for (int64_t k = 0; k < r; ++k) {
+                x[k] += alpha * pp[k];
+                res[k] -= alpha * q[k];
+            }
+            double rs2 = oracle_dot(res, res, r);
+            double beta = rs > 0.0 ? rs2 / rs : 0.0;
+            for (int64_t k = 0; k < r; ++k)
+                pp[k] = res[k] + beta * pp[k];
+            rs = rs2;
+        }
+    }
+    free(start); free(nbr); free(cv); free(w);
     return 0;
 }
