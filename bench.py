@@ -715,6 +715,102 @@ def run_batched(args, rank, world, local_rank):
     return 0
 
 
+def run_als(args, rank, world, local_rank):
+    """ALS with batched CG (Sec. VI-E) on the workload-4 pattern: one sweep
+    = `--cg-iters` CG iterations for A then as many for B; every CG query is
+    one FusedMM over the 0/1 pattern, every CG step's row work one kernel."""
+    import torch
+
+    from paper_2203_07673_gb300 import als, fmm
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    w = make_workload(4, args.scale)
+    S, r = w["S"], w["r"]
+    rp = torch.from_numpy(S.row_ptr).to(dev)
+    ci = torch.from_numpy(S.col_idx).to(dev)
+    c = torch.from_numpy(w["vals"]).to(dev)
+    A0 = torch.from_numpy(w["A"]).to(dev)
+    B0 = torch.from_numpy(w["B"]).to(dev)
+    plan = fmm.Plan(rp, ci, S.n, r)
+    A, B = A0.clone(), B0.clone()
+    lam, iters = args.als_lambda, args.cg_iters
+    solver = als.ALS(plan, c, A, B, lam)
+    loss0 = solver.loss()
+    for _ in range(max(1, args.warmup // 3)):
+        solver.sweep(iters)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    stream = torch.cuda.current_stream()
+    K = args.steps
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(K):
+        solver.sweep(iters)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    sweep_ms = e0.elapsed_time(e1) / K
+    loss1 = solver.loss()
+
+    # breakdown: the FusedMM queries and the CG row updates of one A side
+    q = torch.empty(S.m, r, device=dev)
+    res = torch.empty(S.m, r, device=dev); p = torch.empty(S.m, r, device=dev)
+    rs = torch.ones(S.m, device=dev)
+
+    def time_of(fn, reps=20):
+        fn()
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True); a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(reps):
+            fn()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        return a0.elapsed_time(a1) / reps
+
+    p.copy_(A)
+    t_query_a = time_of(lambda: fmm.fusedmm(plan, None, p, B, out=q))
+    t_update_a = time_of(lambda: fmm.cg_update(lam, A, res, p, q, rs))
+    qn = torch.empty(S.n, r, device=dev); pn = B.clone()
+    t_query_b = time_of(lambda: fmm.fusedmm_t(plan, None, A, pn, out=qn))
+    fused_calls = 2 * (iters + 1)
+    units_sweep = fused_calls * float(S.nnz) * r
+    line = {
+        "metric": METRIC, "value": units_sweep / (sweep_ms / 1e3), "unit": UNIT, "n_gpus": 1,
+        "steps": K, "warmup": args.warmup, "ms_per_step": sweep_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "ALS with CG on " + w["name"], "m": S.m, "n": S.n,
+                   "nnz": S.nnz, "r": r, "lambda": lam, "cg_iters_per_side": iters,
+                   "step": f"one ALS sweep: {iters} CG iterations for A, then {iters} for B; "
+                           f"units = nnz*r per FusedMM query ({fused_calls} per sweep)"},
+        "als": {"loss_before": loss0, "loss_after": loss1,
+                "fusedmm_query_ms_A": t_query_a, "fusedmm_query_ms_B": t_query_b,
+                "cg_row_update_ms_A": t_update_a,
+                "row_update_share": iters * t_update_a / (sweep_ms / 2)},
+        "gpu_launches": K * (2 * (3 + 2 * iters) + (1 if plan.info()["split_rows"] else 0)),
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        import oracle
+        rows = max(256, int(S.m * 0.004))
+        sub = S.rows_slice(0, rows)
+        cols, ci_s = np.unique(sub.col_idx, return_inverse=True)
+        a = w["A"][:rows].astype(np.float64); b = w["B"][cols].astype(np.float64)
+        cv = w["vals"][:sub.nnz].astype(np.float64)
+        t0 = time.perf_counter()
+        oracle.als_cg(sub.row_ptr, ci_s.astype(np.int64), cv, a, b, lam, iters, 0)
+        t = time.perf_counter() - t0
+        line["cpu_baseline"] = {
+            "value": (iters + 1) * sub.nnz * r / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"A-side CG ({iters} iterations) of the first {rows} rows ({sub.nnz} nnz) "
+                      "in FP64, sequential (oracle/fmm_oracle.c)"}
+    print(json.dumps(line), flush=True)
+    plan.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -724,6 +820,9 @@ def main():
     ap.add_argument("--workload", type=int, default=2, choices=[1, 2, 3, 4, 5])
     ap.add_argument("--batch-count", type=int, default=512, help="matrices of workload 5")
     ap.add_argument("--no-tune", action="store_true", help="workload 5 without the autotuner")
+    ap.add_argument("--als", action="store_true", help="ALS with batched CG on workload 4's pattern")
+    ap.add_argument("--als-lambda", type=float, default=0.1)
+    ap.add_argument("--cg-iters", type=int, default=10)
     ap.add_argument("--scale", type=float, default=1.0, help="row-count scale (1 = full)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -740,7 +839,10 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    rc = (run_batched if args.workload == 5 else run_fmm)(args, rank, world, local_rank)
+    if args.als:
+        rc = run_als(args, rank, world, local_rank)
+    else:
+        rc = (run_batched if args.workload == 5 else run_fmm)(args, rank, world, local_rank)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -268,6 +268,31 @@ int fmm_batch_backward(const fmm_batch *batch, fmm_stream stream);
 int fmm_batch_destroy(fmm_batch *batch);
 
 /*
+ * Row-wise conjugate gradients for ALS (Sec. VI-E).  ALS updates every row x_i
+ * of one factor by solving M_i x_i = b_i, M_i x = sum_j <x, Y_j> Y_j +
+ * lambda x, b_i = sum_j c_ij Y_j over the nonzeros of the row (the other
+ * factor Y fixed).  CG runs on all rows at once: the product M p of every row
+ * without the lambda term is one FusedMM over the 0/1 pattern (fmm_fusedmm
+ * with vals = NULL for the A side, fmm_fusedmm_t for the B side), b is one
+ * SpMM of the observed values (fmm_spmm / fmm_spmm_t), and these two calls do
+ * the per-row vector work of a CG step in one kernel.
+ *
+ * All vectors are float32, rows x r, row-major, on the device; rs holds one
+ * float per row.
+ * fmm_cg_init:   res = b - mx - lambda x;  p = res;  rs = <res, res>
+ *                (mx = the FusedMM of x, without the lambda term).
+ * fmm_cg_update: with q = the FusedMM of p (without lambda), t = q + lambda p:
+ *                alpha = rs / <p, t> (0 if <p, t> <= 0);  x += alpha p;
+ *                res -= alpha t;  rs' = <res, res>;  beta = rs' / rs (0 if
+ *                rs = 0);  p = res + beta p;  rs = rs'.
+ * Row reductions are fixed-order warp sums: results are deterministic.
+ */
+int fmm_cg_init(int32_t rows, int32_t r, float lambda, const float *b, const float *mx,
+                const float *x, float *res, float *p, float *rs, fmm_stream stream);
+int fmm_cg_update(int32_t rows, int32_t r, float lambda, float *x, float *res, float *p,
+                  const float *q, float *rs, fmm_stream stream);
+
+/*
  * FusedMMA (same result as fmm_fusedmm) for callers that cannot allocate
  * device memory: no plan, no cudaMalloc, no allocating library call.  The
  * paper has no counterpart; this is an interface for memory-constrained

@@ -18,6 +18,7 @@ Functions (all return float64 numpy arrays):
   fusedmm_grad(rowptr, colidx, vals, A, B, G, n)     -> (dA, dB, ds)
   fusedmm_t_grad(rowptr, colidx, vals, A, B, Gn, n)  -> (dA, dB, ds)
   als_cg(rowptr, colidx, c, A, B, lam, iters, side)  -> updated A (side 0) or B (side 1)
+  gat(rowptr, colidx, vals, f, g, H, heads, slope)   -> out[m, heads * rh]  (GAT forward)
 ``vals=None`` means every value of S is 1.
 """
 from __future__ import annotations
@@ -46,7 +47,7 @@ def build_oracle(force: bool = False) -> str:
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
-           "-o", tmp, _SRC]
+           "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -72,6 +73,8 @@ def _load():
                                       ptr, ptr, ptr, ptr],
             "oracle_als_cg": [i64, i64, i64, ptr, ptr, ptr, ptr, ptr, ctypes.c_double,
                               i64, ctypes.c_int],
+            "oracle_gat": [i64, i64, i64, i64, ptr, ptr, ptr, ptr, ptr, ptr, ctypes.c_double,
+                           ptr],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -202,3 +205,20 @@ def als_cg(rowptr, colidx, c, A, B, lam, iters, side):
     _run(_load().oracle_als_cg, m, n, r, _p(rowptr), _p(colidx), _p(c), _p(A), _p(B),
          float(lam), int(iters), int(side))
     return A if side == 0 else B
+
+
+def gat(rowptr, colidx, vals, f, g, H, heads, slope):
+    """Multi-head graph-attention forward (Sec. VI-E): f (m x heads), g
+    (n x heads), H (n x heads*rh); returns out (m x heads*rh)."""
+    rowptr, colidx = _i64(rowptr), _i64(colidx)
+    m = rowptr.shape[0] - 1
+    f = _f64(f).reshape(m, heads)
+    H = _f64(H)
+    n = H.shape[0]
+    g = _f64(g).reshape(n, heads)
+    r = H.shape[1]
+    rh = r // heads
+    out = np.zeros((m, r))
+    _run(_load().oracle_gat, m, n, heads, rh, _p(rowptr), _p(colidx), _p(_f64(vals)),
+         _p(f), _p(g), _p(H), float(slope), _p(out))
+    return out

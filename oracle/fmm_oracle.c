@@ -29,13 +29,14 @@
  *   Sec. IV-A               per-nonzero SpMMA update A_i += S_ij B_j
  *   Sec. IV-B               row form FusedMMA_i = sum_j S_ij <A_i, B_j> B_j
  *   Sec. VI-E               ALS: per-row least squares M x = b solved by CG,
- *                           the queries M x batched as FusedMM
+ *                           the queries M x batched as FusedMM; GAT: the
+ *                           attention variant of SDDMM, softmax, aggregation
  * The gradients are not in the paper; they are the derivatives of the
  * scalar L = <G, FusedMM(S, A, B)> with respect to A, B and the values of S,
  * on a fixed pattern.
  *
  * Built as a shared library by oracle/build.py:
- *   gcc -O2 -fopenmp -fPIC -shared -o oracle/_build/liboracle.so oracle/fmm_oracle.c
+ *   gcc -O2 -fopenmp -fPIC -shared -lm -o oracle/_build/liboracle.so oracle/fmm_oracle.c
  * Rows are independent in the row-wise routines, so those loop over rows with
  * an OpenMP parallel-for; the scatter routines run sequentially.
  */
@@ -356,5 +357,60 @@ int oracle_als_cg(int64_t m, int64_t n, int64_t r, const int64_t *rowptr,
         }
     }
     free(start); free(nbr); free(cv); free(w);
+    return 0;
+}
+
+/* ---------------------------------------------------------------------------
+ * Graph-attention layer, forward (Sec. VI-E, GAT workload).
+ *
+ * One attention head replaces S by S' = LeakyReLU(S * (H .GAT H^T)) with
+ * (H .GAT H^T)_ij = a^T (H_i || H_j) = a_l^T H_i + a_r^T H_j, normalises each
+ * row of S' with a softmax over its nonzeros and aggregates the rows of H:
+ *     e_ij  = LeakyReLU(s_ij * (f_i + g_j)),  f = H_dst a_l,  g = H a_r
+ *     alpha = softmax over the nonzeros of row i of e_ij
+ *     out_i = sum_j alpha_ij H_j
+ * Multi-head: `heads` independent heads, head h using columns
+ * [h * rh, (h + 1) * rh) of H (n x heads*rh) and out (m x heads*rh), and
+ * f[i * heads + h], g[j * heads + h].  LeakyReLU(x) = x if x > 0 else
+ * slope * x.  Rows without nonzeros give zeros.  Softmax in the textbook
+ * two-pass form: max, then sum of exp(e - max).  Rows in parallel.
+ * ------------------------------------------------------------------------ */
+#include <math.h>
+
+int oracle_gat(int64_t m, int64_t n, int64_t heads, int64_t rh, const int64_t *rowptr,
+               const int64_t *colidx, const double *vals, const double *f, const double *g,
+               const double *H, double slope, double *out)
+{
+    if (oracle_check(m, n, rowptr, colidx))
+        return -1;
+    const int64_t r = heads * rh;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < m; ++i) {
+        for (int64_t k = 0; k < r; ++k)
+            out[i * r + k] = 0.0;
+        for (int64_t h = 0; h < heads; ++h) {
+            double mx = -INFINITY;
+            for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+                double x = oracle_s(vals, p) * (f[i * heads + h] + g[colidx[p] * heads + h]);
+                double e = x > 0.0 ? x : slope * x;
+                if (e > mx)
+                    mx = e;
+            }
+            double sum = 0.0;
+            for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+                double x = oracle_s(vals, p) * (f[i * heads + h] + g[colidx[p] * heads + h]);
+                double e = x > 0.0 ? x : slope * x;
+                sum += exp(e - mx);
+            }
+            for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+                double x = oracle_s(vals, p) * (f[i * heads + h] + g[colidx[p] * heads + h]);
+                double e = x > 0.0 ? x : slope * x;
+                double a = exp(e - mx) / sum;
+                const double *hj = H + colidx[p] * r + h * rh;
+                for (int64_t k = 0; k < rh; ++k)
+                    out[i * r + h * rh + k] += a * hj[k];
+            }
+        }
+    }
     return 0;
 }

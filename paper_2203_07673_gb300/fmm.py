@@ -38,6 +38,8 @@ _SIGNATURES = {
     "fmm_fusedmm_t_bwd": ([_P, _P, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "fmm_fusedmm_noalloc": ([_P, _I32, _I32, _P, _P, _P, _P, _P], ctypes.c_int),
     "fmm_plan_set_variant": ([_P, _I32, _I32], ctypes.c_int),
+    "fmm_cg_init": ([_I32, _I32, ctypes.c_float, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
+    "fmm_cg_update": ([_I32, _I32, ctypes.c_float, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "fmm_batch_create": ([_P, _I32, _P, _P], ctypes.c_int),
     "fmm_batch_forward": ([_P, _P], ctypes.c_int),
     "fmm_batch_backward": ([_P, _P], ctypes.c_int),
@@ -356,3 +358,27 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def _rows_f32(t, rows, r, name):
+    return _ptr(t, name, torch.float32, (rows, r))
+
+
+def cg_init(lam, b, mx, x, res, p, rs, stream=None):
+    """fmm_cg_init on float32 row blocks (rows x r)."""
+    rows, r = x.shape
+    rc = lib().fmm_cg_init(rows, r, float(lam), _rows_f32(b, rows, r, "b"),
+                           _rows_f32(mx, rows, r, "mx"), _rows_f32(x, rows, r, "x"),
+                           _rows_f32(res, rows, r, "res"), _rows_f32(p, rows, r, "p"),
+                           _ptr(rs, "rs", torch.float32, (rows,)), _stream(stream))
+    _check(rc, "fmm_cg_init")
+
+
+def cg_update(lam, x, res, p, q, rs, stream=None):
+    """fmm_cg_update on float32 row blocks (rows x r)."""
+    rows, r = x.shape
+    rc = lib().fmm_cg_update(rows, r, float(lam), _rows_f32(x, rows, r, "x"),
+                             _rows_f32(res, rows, r, "res"), _rows_f32(p, rows, r, "p"),
+                             _rows_f32(q, rows, r, "q"), _ptr(rs, "rs", torch.float32, (rows,)),
+                             _stream(stream))
+    _check(rc, "fmm_cg_update")
