@@ -38,7 +38,7 @@ UNIT = "nnz*r/s"
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "roofline_traffic.txt")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2203_07673_gb300", "csrc", f)
                   for f in ("fmm_rows.cuh", "fmm_rows_f32.cu", "fmm_rows_bf16.cu",
-                            "fmm_internal.cuh")]
+                            "fmm_internal.cuh", "fmm_plan.cu")]
 
 
 def kernel_source_sha() -> str:
@@ -811,6 +811,82 @@ def run_als(args, rank, world, local_rank):
     return 0
 
 
+def run_gat(args, rank, world, local_rank):
+    """Graph-attention forward (Sec. VI-E) on an R-MAT 2^22 graph (avg degree
+    16, the workload-3 recipe drawn on the device), `--heads` heads of
+    `--head-dim` features, random weights as in the paper."""
+    import torch
+
+    from paper_2203_07673_gb300 import fmm, gat
+    from paper_2203_07673_gb300 import workloads as wl
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    scale = 22
+    while scale > 8 and (1 << scale) > (1 << 22) * args.scale:
+        scale -= 1
+    nv = 1 << scale
+    gen = wl._torch_gen(dev, wl.ROOT_SEED + 3)
+    rp, ci = wl.rmat_torch(scale, 16 * nv, 0.57, 0.19, 0.19, gen, dev, nv)
+    heads, rh = args.heads, args.head_dim
+    r = heads * rh
+    tdt = torch.bfloat16 if args.gat_bf16 else torch.float32
+    plan = fmm.Plan(rp, ci, nv, r, tdt)
+    X = torch.randn(nv, r, device=dev, generator=gen)
+    W = torch.randn(r, r, device=dev, generator=gen) / r ** 0.5
+    a_l = torch.randn(r, device=dev, generator=gen)
+    a_r = torch.randn(r, device=dev, generator=gen)
+    H = X @ W
+    f = fmm.gat_project(H, a_l, heads)
+    g = fmm.gat_project(H, a_r, heads)
+    Hp = H.to(tdt).contiguous()
+    out = torch.empty(nv, r, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True); a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(reps):
+            fn()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        return a0.elapsed_time(a1) / reps
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    attn_ms = timed(lambda: fmm.gat_forward(plan, heads, None, f, g, Hp, 0.2, out=out), args.steps)
+    clk = clocks.stop()
+    layer_ms = timed(lambda: gat.gat_layer(plan, X, W, a_l, a_r, heads), max(3, args.steps // 4))
+    nnz = ci.numel()
+    e = 4 if tdt == torch.float32 else 2
+    model = 4 * (nv + 1) + 4 * nnz + nnz * (r * e + 4 * heads) + nv * (4 * heads + 4 * r)
+    peak, peak_kind = load_peaks()
+    line = {
+        "metric": METRIC, "value": nnz * r / (attn_ms / 1e3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": 3, "ms_per_step": attn_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" + (" (bf16 H)" if tdt == torch.bfloat16 else ""), "data": "synthetic",
+        "config": {"workload": f"GAT forward, R-MAT 2^{scale} (a,b,c,d)=(.57,.19,.19,.05), avg "
+                               f"degree 16, {heads} heads x {rh}", "nnz": nnz, "r": r,
+                   "step": "fmm_gat_forward (scores, row softmax, aggregation); units = nnz*r"},
+        "roofline": {"bound": "hbm", "kernel": "gat_kernel", "achieved": model / (attn_ms / 1e3) / 1e9,
+                     "peak": peak, "unit": "GB/s",
+                     "frac": model / (attn_ms / 1e3) / 1e9 / peak, "traffic": None,
+                     "peak_kind": f"{peak_kind} copy bandwidth",
+                     "bytes_model": "CSR + one H row and the head scores g_j per nonzero + f_i "
+                                    "and the output row per row"},
+        "gat": {"attention_ms": attn_ms, "layer_ms": layer_ms,
+                "layer": "X W (torch.matmul) + projections + attention"},
+        "gpu_launches": args.steps, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    plan.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -823,6 +899,10 @@ def main():
     ap.add_argument("--als", action="store_true", help="ALS with batched CG on workload 4's pattern")
     ap.add_argument("--als-lambda", type=float, default=0.1)
     ap.add_argument("--cg-iters", type=int, default=10)
+    ap.add_argument("--gat", action="store_true", help="graph-attention forward on an R-MAT graph")
+    ap.add_argument("--heads", type=int, default=4)
+    ap.add_argument("--head-dim", type=int, default=32)
+    ap.add_argument("--gat-bf16", action="store_true")
     ap.add_argument("--scale", type=float, default=1.0, help="row-count scale (1 = full)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -841,6 +921,8 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     if args.als:
         rc = run_als(args, rank, world, local_rank)
+    elif args.gat:
+        rc = run_gat(args, rank, world, local_rank)
     else:
         rc = (run_batched if args.workload == 5 else run_fmm)(args, rank, world, local_rank)
     if world > 1:

@@ -149,6 +149,18 @@ int fmm_plan_create(const fmm_csr *S, int32_t r, int32_t dtype,
                     const fmm_plan_options *options, fmm_stream stream,
                     fmm_plan **plan);
 
+/*
+ * Registers values that will not change: copies them once into the order of
+ * S^T (a permutation pass, queued on the stream; allocates nnz floats on the
+ * first call).  Later calls that pass this same vals pointer skip the
+ * per-call permutation of their passes over S^T (fmm_fusedmm_t, fmm_spmm_t
+ * with v = vals, the backward passes over S^T) and read the stored copy, so
+ * the contents must not change while registered: call again after changing
+ * them (or with vals = NULL to forget them).  Values passed through any
+ * other pointer are permuted per call as usual.
+ */
+int fmm_plan_set_values(fmm_plan *plan, const float *vals, fmm_stream stream);
+
 /* Frees a plan and its workspace (synchronises the device first).  NULL is a
  * no-op. */
 int fmm_plan_destroy(fmm_plan *plan);
@@ -291,6 +303,26 @@ int fmm_cg_init(int32_t rows, int32_t r, float lambda, const float *b, const flo
                 const float *x, float *res, float *p, float *rs, fmm_stream stream);
 int fmm_cg_update(int32_t rows, int32_t r, float lambda, float *x, float *res, float *p,
                   const float *q, float *rs, fmm_stream stream);
+
+/*
+ * Graph-attention layer, forward (Sec. VI-E, the GAT workload): the attention
+ * variant of SDDMM feeding a softmax-normalised SpMM.  For every head h
+ * (heads must divide the plan's r; head h owns columns [h*rh, (h+1)*rh) with
+ * rh = r / heads) and nonzero (i, j):
+ *   e_ij = LeakyReLU(s_ij (f_i + g_j))       (LeakyReLU(x) = x > 0 ? x : slope x)
+ *   out_i = sum_j softmax_j(e_i.)_j  H_j      (softmax over the nonzeros of row i)
+ * f (m x heads) and g (n x heads) are the per-node projections a_l^T H_i and
+ * a_r^T H_j that make up the paper's a^T (H_i || H_j); H (n x r) of the
+ * plan's dtype; out (m x r) float32; vals NULL = all ones.  Rows without
+ * nonzeros give zeros.  One gather pass per row with an online softmax.
+ */
+int fmm_gat_forward(const fmm_plan *plan, int32_t heads, const float *vals, const float *f,
+                    const float *g, const void *H, float slope, float *out, fmm_stream stream);
+
+/* out[i, h] = sum_k X[i, h*rh + k] w[h*rh + k]  (rows x heads, float32): the
+ * per-node projections f and g of fmm_gat_forward. */
+int fmm_gat_project(int32_t rows, int32_t heads, int32_t rh, const float *X, const float *w,
+                    float *out, fmm_stream stream);
 
 /*
  * FusedMMA (same result as fmm_fusedmm) for callers that cannot allocate

@@ -216,9 +216,10 @@ def gat(rowptr, colidx, vals, f, g, H, heads, slope):
     H = _f64(H)
     n = H.shape[0]
     g = _f64(g).reshape(n, heads)
+    vals = _f64(vals)          # kept alive across the call
     r = H.shape[1]
     rh = r // heads
     out = np.zeros((m, r))
-    _run(_load().oracle_gat, m, n, heads, rh, _p(rowptr), _p(colidx), _p(_f64(vals)),
+    _run(_load().oracle_gat, m, n, heads, rh, _p(rowptr), _p(colidx), _p(vals),
          _p(f), _p(g), _p(H), float(slope), _p(out))
     return out

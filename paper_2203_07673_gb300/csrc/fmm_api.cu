@@ -112,10 +112,15 @@ int run_pass(const fmm_plan *p, const Side &side, int mode, const float *s, cons
     a.r = p->r;
     cudaError_t e = cudaSuccess;
     if (side.perm && s) {
-        // values of S gathered once into the order of S^T, so the pass
-        // streams them instead of fetching one scattered word per nonzero
-        e = launch_permute(s, side.perm, p->vals_t, p->nnz, st);
-        a.s = p->vals_t;
+        if (s == p->static_src && p->vals_static) {
+            // registered values: their S^T-order copy is already there
+            a.s = p->vals_static;
+        } else {
+            // values of S gathered once into the order of S^T, so the pass
+            // streams them instead of fetching one scattered word per nonzero
+            e = launch_permute(s, side.perm, p->vals_t, p->nnz, st);
+            a.s = p->vals_t;
+        }
         a.s_direct = 1;
     }
     if (e == cudaSuccess)
@@ -177,6 +182,30 @@ int fmm_plan_create(const fmm_csr *S, int32_t r, int32_t dtype, const fmm_plan_o
     }
     CHECK(validate_csr(S, (cudaStream_t)stream, nullptr));
     return create_plan(S, r, dtype, options, (cudaStream_t)stream, plan);
+}
+
+int fmm_plan_set_values(fmm_plan *p, const float *vals, fmm_stream stream)
+{
+    CHECK(check_plan(p));
+    p->static_src = nullptr;
+    if (!vals || !p->has_t || p->nnz == 0)
+        return FMM_OK;
+    if (!p->vals_static) {
+        cudaError_t e = cudaMalloc(&p->vals_static, sizeof(float) * (size_t)p->nnz);
+        if (e != cudaSuccess) {
+            p->vals_static = nullptr;
+            set_error("allocate registered values", e);
+            return e == cudaErrorMemoryAllocation ? FMM_ENOMEM : FMM_ECUDA;
+        }
+        p->workspace_bytes += (int64_t)sizeof(float) * p->nnz;
+    }
+    cudaError_t e = launch_permute(vals, p->perm_t, p->vals_static, p->nnz, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        set_error("fmm_plan_set_values", e);
+        return FMM_ECUDA;
+    }
+    p->static_src = vals;
+    return FMM_OK;
 }
 
 int fmm_plan_destroy(fmm_plan *plan)

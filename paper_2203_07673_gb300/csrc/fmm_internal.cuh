@@ -32,7 +32,8 @@ struct Side {
     int4 *chunks = nullptr;           // {row, begin, end, unused} per chunk
     int32_t n_chunks = 0;
     int4 *split = nullptr;            // {row, first chunk, chunk count, unused}
-    float *partials = nullptr;        // n_chunks x r partial rows
+    float *partials = nullptr;        // 3 x n_chunks x r floats: partial rows (and
+                                      // the attention pass's softmax states)
     int32_t max_nnz = 0;              // longest row
     KernelVariant variant;            // kernel variant of passes over this side
     std::vector<int32_t> bucket_start;  // host: first position in `order` of
@@ -146,6 +147,8 @@ struct fmm_plan {
     int32_t *col_idx_t = nullptr;
     int32_t *perm_t = nullptr;
     float *vals_t = nullptr;          // per-call values permuted into S^T order
+    const float *static_src = nullptr;  // values registered by fmm_plan_set_values
+    float *vals_static = nullptr;       // ... and their copy in S^T order
     int64_t workspace_bytes = 0;
     int device = 0;
 };

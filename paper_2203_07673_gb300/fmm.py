@@ -38,6 +38,9 @@ _SIGNATURES = {
     "fmm_fusedmm_t_bwd": ([_P, _P, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "fmm_fusedmm_noalloc": ([_P, _I32, _I32, _P, _P, _P, _P, _P], ctypes.c_int),
     "fmm_plan_set_variant": ([_P, _I32, _I32], ctypes.c_int),
+    "fmm_plan_set_values": ([_P, _P, _P], ctypes.c_int),
+    "fmm_gat_forward": ([_P, _I32, _P, _P, _P, _P, ctypes.c_float, _P, _P], ctypes.c_int),
+    "fmm_gat_project": ([_I32, _I32, _I32, _P, _P, _P, _P], ctypes.c_int),
     "fmm_cg_init": ([_I32, _I32, ctypes.c_float, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "fmm_cg_update": ([_I32, _I32, ctypes.c_float, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "fmm_batch_create": ([_P, _I32, _P, _P], ctypes.c_int),
@@ -177,6 +180,14 @@ class Plan:
         """fmm_plan_set_variant (0 leaves a side unchanged)."""
         _check(lib().fmm_plan_set_variant(self.handle, int(variant), int(variant_t)),
                "fmm_plan_set_variant")
+
+    def set_values(self, vals, stream=None):
+        """fmm_plan_set_values: register values that stay unchanged (None
+        forgets them); keeps a reference to the tensor."""
+        self._static_vals = vals
+        rc = lib().fmm_plan_set_values(self.handle, self._f32(vals, (self.nnz,), "vals"),
+                                       _stream(stream))
+        _check(rc, "fmm_plan_set_values")
 
     def info(self) -> dict:
         inf = _Info()
@@ -382,3 +393,27 @@ def cg_update(lam, x, res, p, q, rs, stream=None):
                              _rows_f32(q, rows, r, "q"), _ptr(rs, "rs", torch.float32, (rows,)),
                              _stream(stream))
     _check(rc, "fmm_cg_update")
+
+
+def gat_project(X, w, heads, out=None, stream=None):
+    """fmm_gat_project: per-head projections X[:, head] . w[head] (float32)."""
+    rows, r = X.shape
+    if out is None:
+        out = torch.empty(rows, heads, dtype=torch.float32, device=X.device)
+    rc = lib().fmm_gat_project(rows, heads, r // heads, _ptr(X, "X", torch.float32, (rows, r)),
+                               _ptr(w, "w", torch.float32, (r,)),
+                               _ptr(out, "out", torch.float32, (rows, heads)), _stream(stream))
+    _check(rc, "fmm_gat_project")
+    return out
+
+
+def gat_forward(plan: Plan, heads, vals, f, g, H, slope=0.2, out=None, stream=None):
+    """fmm_gat_forward: attention scores, row softmax and aggregation."""
+    out = _out(out, (plan.m, plan.r), plan)
+    rc = lib().fmm_gat_forward(plan.handle, int(heads), plan._f32(vals, (plan.nnz,), "vals"),
+                               plan._f32(f, (plan.m, heads), "f"),
+                               plan._f32(g, (plan.n, heads), "g"), plan._dense(H, plan.n, "H"),
+                               float(slope), plan._f32(out, (plan.m, plan.r), "out"),
+                               _stream(stream))
+    _check(rc, "fmm_gat_forward")
+    return out

@@ -272,3 +272,34 @@ def test_plan_info_reports_schedule():
     assert info["max_row_nnz"] == deg.max() and info["max_col_nnz"] == cdeg.max()
     assert info["split_rows"] == (deg > 64).sum() and info["split_cols"] == (cdeg > 64).sum()
     assert info["row_chunks"] == int(np.ceil(deg[deg > 64] / 64).sum())
+
+
+@pytest.mark.parametrize("offset", [0, 1], ids=["aligned", "unaligned"])
+def test_value_permutation_large_unaligned(offset):
+    """FusedMMB gathers the values of S into the order of S^T before its
+    pass (four per thread in blocks of 1024); over 2^20 nonzeros, a ragged
+    tail and values that are not 16-byte aligned, the result must match the
+    oracle, and registered values must give the same bits."""
+    from paper_2203_07673_gb300 import fmm
+    rng = np.random.default_rng(11 + offset)
+    m, n = 40000, 30000
+    S = wl.random_csr(m, n, rng, mean_deg=27, empty_frac=0.02, unsorted=True, hubs=((2, 5000),))
+    assert S.nnz >= 1 << 20 and (offset or S.nnz % 4 != 0)   # a ragged tail when aligned
+    r = 8
+    A = rng.standard_normal((m, r)).astype(np.float32)
+    B = rng.standard_normal((n, r)).astype(np.float32)
+    vals = rng.uniform(0.5, 1.5, S.nnz).astype(np.float32)
+    rp, ci, _, At, Bt = upload(S, None, A, B)
+    buf = torch.zeros(S.nnz + 1, device="cuda")
+    buf[offset:offset + S.nnz] = torch.from_numpy(vals).cuda()
+    vt = buf[offset:offset + S.nnz]
+    plan = fmm.Plan(rp, ci, n, r)
+    got = fmm.fusedmm_t(plan, vt, At, Bt)
+    ref = oracle.fusedmm_t(S.row_ptr, S.col_idx, vals, A, B, n)
+    mag = oracle.fusedmm_t(S.row_ptr, S.col_idx, vals, np.abs(A), np.abs(B), n)
+    cdeg = int(np.bincount(S.col_idx, minlength=n).max())
+    assert_close("fusedmm_t (staged values)", got, ref, mag, r, cdeg)
+    # registered values take the same two passes
+    plan.set_values(vt)
+    assert torch.equal(fmm.fusedmm_t(plan, vt, At, Bt), got)
+    plan.set_values(None)

@@ -78,3 +78,16 @@ def test_leaky_slope_matters_only_for_negative_scores():
     np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-12)
     c = oracle.gat(S.row_ptr, S.col_idx, vals, -fpos, -gpos, H, 2, 0.01)
     assert not np.allclose(a, c)
+
+
+def test_float32_inputs_match_float64_inputs():
+    # the loader widens float32 arrays to float64 copies; those copies must
+    # live through the call (float32 and float64 inputs give the same result)
+    S, vals, f, g, H = _problem(6)
+    a = oracle.gat(S.row_ptr, S.col_idx, vals, f, g, H, 2, 0.2)
+    b = oracle.gat(S.row_ptr, S.col_idx, vals.astype(np.float32).astype(np.float64),
+                   f.astype(np.float32), g.astype(np.float32), H.astype(np.float32), 2, 0.2)
+    c = oracle.gat(S.row_ptr, S.col_idx, vals.astype(np.float32), f.astype(np.float32),
+                   g.astype(np.float32), H.astype(np.float32), 2, 0.2)
+    np.testing.assert_array_equal(b, c)
+    np.testing.assert_allclose(a, c, rtol=1e-5, atol=1e-6)
