@@ -41,9 +41,13 @@ KERNEL_SOURCES = [os.path.join(ROOT, "paper_2203_07673_gb300", "csrc", f)
                             "fmm_internal.cuh", "fmm_plan.cu")]
 
 
-def kernel_source_sha() -> str:
+GAT_SOURCES = [os.path.join(ROOT, "paper_2203_07673_gb300", "csrc", f)
+               for f in ("fmm_gat.cu", "fmm_rows.cuh", "fmm_internal.cuh", "fmm_plan.cu")]
+
+
+def kernel_source_sha(call: str = "") -> str:
     h = hashlib.sha1()
-    for f in KERNEL_SOURCES:
+    for f in (GAT_SOURCES if call == "fmm_gat_forward" else KERNEL_SOURCES):
         with open(f, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
@@ -53,7 +57,7 @@ def read_traffic(workload, call, dtype):
     """DRAM bytes per call from profiles/roofline_traffic.txt, if captured on
     the current kernel sources; else (None, reason)."""
     try:
-        sha = kernel_source_sha()
+        sha = kernel_source_sha(call)
         with open(PROFILE_TRAFFIC) as fh:
             for line in fh:
                 if line.startswith("#") or "|" not in line:
@@ -75,21 +79,39 @@ def gather_model_bytes(m, nnz, r, e, vals=True):
     return 4 * (m + 1) + 4 * nnz + (4 * nnz if vals else 0) + m * r * e + nnz * r * e + 4 * m * r
 
 
+def compulsory_model_bytes(m, n, nnz, r, e, vals=True):
+    """The same pass if every dense row were read from DRAM once: the
+    gathers are replaced by the n x r x e bytes of the gathered matrix."""
+    return 4 * (m + 1) + 4 * nnz + (4 * nnz if vals else 0) + m * r * e + n * r * e + 4 * m * r
+
+
+NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e, nominal
+
+
 def permute_bytes(nnz):
     """Values of S into S^T order: perm read, one value fetched, one written."""
     return 12 * nnz
 
 
-def step_calls(k, S, r, e, vals_given):
-    """(name, model bytes) of the calls of one step of workload k."""
-    m, n, nnz = S.m, S.n, S.nnz
-    fwd = gather_model_bytes(m, nnz, r, e, vals_given)
-    fwd_t = gather_model_bytes(n, nnz, r, e, vals_given) + (permute_bytes(nnz) if vals_given else 0)
+def gather_model_bytes_mn(m, n, nnz, r, e, vals=True):
+    return gather_model_bytes(m, nnz, r, e, vals)
+
+
+def step_calls(k, S, r, e, vals_given, model=gather_model_bytes_mn):
+    """(name, model bytes) of the calls of one step of workload k, by the
+    gather model (default) or compulsory_model_bytes."""
+    return _calls(k, S.m, S.n, S.nnz, r, e, vals_given, model)
+
+
+def _calls(k, m, n, nnz, r, e, vals_given, model):
+    fwd = model(m, n, nnz, r, e, vals_given)
+    fwd_t = model(n, m, nnz, r, e, vals_given) + (permute_bytes(nnz) if vals_given else 0)
     if k == 3:
         # backward: pass over S (A_i, G_i local, B_j gathered, dA and ds written),
         # pass over S^T (B_j local, A_i and G_i gathered, dB written)
-        p1 = gather_model_bytes(m, nnz, r, e, True) + 4 * m * r + 4 * nnz
-        p2 = gather_model_bytes(n, nnz, r, e, True) + 4 * nnz * r + permute_bytes(nnz)
+        p1 = model(m, n, nnz, r, e, True) + 4 * m * r + 4 * nnz
+        g_rows = nnz if model is gather_model_bytes_mn else m   # G_i with each gathered A_i
+        p2 = model(n, m, nnz, r, e, True) + 4 * g_rows * r + permute_bytes(nnz)
         return [("fmm_fusedmm", fwd), ("fmm_fusedmm_bwd", p1 + p2)]
     return [("fmm_fusedmm", fwd), ("fmm_fusedmm_t", fwd_t)]
 
@@ -214,13 +236,25 @@ def oracle_sample(w, seconds: float, rows_hint: int | None = None):
     if rows_hint is None:
         rows = int(min(S.m, max(rows, rows * seconds / max(t, 1e-6))))
         t, nnz, ncols = run(rows)
-    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    threads = oracle.threads()
     what = ("FusedMMA forward (rows on {t} OpenMP threads) + its gradient (sequential)"
             if fwd_bwd else "FusedMMA (rows on {t} OpenMP threads) + FusedMMB (sequential scatter)")
     desc = (f"first {rows} of {S.m} rows ({nnz} nnz, {nnz / max(S.nnz, 1):.2%} of the "
             f"workload), columns remapped to the {ncols} they touch; "
             + what.format(t=threads) + " in FP64 (oracle/fmm_oracle.c)")
     return (1.0 if fwd_bwd else 2.0) * nnz * r / t, desc, threads, rows
+
+
+def single_thread_oracle(w, seconds):
+    """The oracle sample again on one thread (a smaller sample)."""
+    import oracle
+    before = oracle.threads()
+    try:
+        oracle.threads(1)
+        v, _, _, rows = oracle_sample(w, seconds)
+    finally:
+        oracle.threads(before)
+    return {"single_thread_value": v, "single_thread_rows": rows}
 
 
 def _bf16_round(x):
@@ -308,6 +342,34 @@ def run_reference(args, rank, world):
     return 0
 
 
+def cusparse_forward(rp, ci, vals, A, B, S, r, fused_out, timed):
+    """FusedMMA by library calls for comparison: the cuSPARSE SDDMM and SpMM
+    behind torch.sparse (sampled_addmm, then the values scaled by s, then a
+    CSR x dense product), timed like the fused call, checked against it."""
+    import torch
+    if A.dtype != torch.float32:
+        return {"unavailable": "library SDDMM is run for float32 inputs only"}
+    try:
+        ones = torch.ones(S.nnz, device=A.device) if vals is None else vals
+        zero = torch.sparse_csr_tensor(rp, ci, torch.zeros_like(ones), size=(S.m, S.n))
+        Bt = B.t()
+
+        def step():
+            d = torch.sparse.sampled_addmm(zero, A, Bt, beta=0.0, alpha=1.0)
+            v = torch.sparse_csr_tensor(d.crow_indices(), d.col_indices(),
+                                        d.values() * ones, size=(S.m, S.n))
+            return torch.sparse.mm(v, B)
+
+        got = step()
+        rel = float((got - fused_out).norm() / fused_out.norm().clamp_min(1e-30))
+        ms = timed(step)
+        return {"what": "torch.sparse.sampled_addmm (cuSPARSE SDDMM) + values * s + "
+                        "torch.sparse.mm (cuSPARSE SpMM), FusedMMA only",
+                "ms": ms, "rel_diff_vs_fused": rel}
+    except Exception as ex:  # a library without these CUDA kernels
+        return {"unavailable": f"{type(ex).__name__}: {str(ex).splitlines()[0][:160]}"}
+
+
 def workload_config(w, args):
     S = w["S"]
     step = ("FusedMMA forward + backward (dA, dB, ds); units = nnz*r per step"
@@ -369,6 +431,7 @@ def run_fmm(args, rank, world, local_rank):
             fmm.fusedmm_t(plan, vals, A, B, out=out_t)
 
     calls = step_calls(k, S, r, e, vals is not None)
+    calls_comp = step_calls(k, S, r, e, vals is not None, compulsory_model_bytes)
     fns = [call_fwd, call_second]
 
     def barrier():
@@ -457,6 +520,8 @@ def run_fmm(args, rank, world, local_rank):
             ds_h.copy_(ds, non_blocking=True)
 
     e2e_ms = timed(e2e_step, max(3, min(K, 30)))
+    library_fwd = None if args.no_library else cusparse_forward(
+        rp, ci, vals, A, B, S, r, out, lambda fn: timed(fn, max(3, min(K, 20))))
     unfused_ms, fused_ms, e2e_ms = reduce_max([unfused_ms, fused_ms, e2e_ms], dev, world)
 
     units_step = (1.0 if k == 3 else 2.0) * S.nnz * r
@@ -490,10 +555,16 @@ def run_fmm(args, rank, world, local_rank):
             "call_ms": call_ms[dom],
             "dram_frac": None if traffic is None else traffic / (call_ms[dom] / 1e3) / 1e9 / peak,
             "traffic_note": traffic_note,
+            "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
+            "nominal_peak": NOMINAL_HBM_GBS,
+            "compulsory_bytes_per_call": calls_comp[dom][1],
+            "compulsory_frac": calls_comp[dom][1] / (call_ms[dom] / 1e3) / 1e9 / peak,
         },
         "calls": {name: {"ms": call_ms[c], "model_bytes": b,
-                         "model_GBs": b / (call_ms[c] / 1e3) / 1e9}
+                         "model_GBs": b / (call_ms[c] / 1e3) / 1e9,
+                         "compulsory_bytes": calls_comp[c][1]}
                   for c, (name, b) in enumerate(calls)},
+        "library_unfused": library_fwd,
         "fused_vs_unfused": None if k == 3 else {
             "fused_ms": fused_ms, "unfused_ms": unfused_ms,
             "speedup": unfused_ms / fused_ms,
@@ -516,6 +587,7 @@ def run_fmm(args, rank, world, local_rank):
         cv, desc, threads, _ = oracle_sample(w, args.cpu_seconds)
         line["cpu_baseline"] = {"value": cv, "unit": UNIT, "cores": threads, "kind": "oracle",
                                 "sample": desc}
+        line["cpu_baseline"].update(single_thread_oracle(w, args.cpu_seconds / 4))
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()
@@ -737,7 +809,7 @@ def run_als(args, rank, world, local_rank):
     lam, iters = args.als_lambda, args.cg_iters
     solver = als.ALS(plan, c, A, B, lam)
     loss0 = solver.loss()
-    for _ in range(max(1, args.warmup // 3)):
+    for _ in range(max(3, args.warmup)):
         solver.sweep(iters)
     torch.cuda.synchronize()
     clocks = ClockSampler(local_rank)
@@ -777,6 +849,26 @@ def run_als(args, rank, world, local_rank):
     t_query_b = time_of(lambda: fmm.fusedmm_t(plan, None, A, pn, out=qn))
     fused_calls = 2 * (iters + 1)
     units_sweep = fused_calls * float(S.nnz) * r
+
+    # end to end: c, A and B from pinned host memory, one sweep, the factors
+    # read back
+    c_h, A_h, B_h = c.cpu().pin_memory(), A0.cpu().pin_memory(), B0.cpu().pin_memory()
+    Ao_h, Bo_h = torch.empty_like(A_h).pin_memory(), torch.empty_like(B_h).pin_memory()
+
+    def e2e_step():
+        c.copy_(c_h, non_blocking=True)
+        A.copy_(A_h, non_blocking=True)
+        B.copy_(B_h, non_blocking=True)
+        solver.sweep(iters)
+        Ao_h.copy_(A, non_blocking=True)
+        Bo_h.copy_(B, non_blocking=True)
+
+    e2e_ms = time_of(e2e_step, max(3, K))
+    h2d = (c_h.numel() + A_h.numel() + B_h.numel()) * 4
+    d2h = (Ao_h.numel() + Bo_h.numel()) * 4
+    peak, peak_kind = load_peaks()
+    q_bytes = gather_model_bytes(S.m, S.nnz, r, 4, vals=False)
+    traffic, traffic_note = read_traffic(w["name"], "fmm_fusedmm (pattern only)", "f32")
     line = {
         "metric": METRIC, "value": units_sweep / (sweep_ms / 1e3), "unit": UNIT, "n_gpus": 1,
         "steps": K, "warmup": args.warmup, "ms_per_step": sweep_ms, "higher_is_better": True,
@@ -789,7 +881,22 @@ def run_als(args, rank, world, local_rank):
                 "fusedmm_query_ms_A": t_query_a, "fusedmm_query_ms_B": t_query_b,
                 "cg_row_update_ms_A": t_update_a,
                 "row_update_share": iters * t_update_a / (sweep_ms / 2)},
-        "gpu_launches": K * (2 * (3 + 2 * iters) + (1 if plan.info()["split_rows"] else 0)),
+        "roofline": {"bound": "hbm", "kernel": "fmm_fusedmm (CG query M p, pattern only)",
+                     "achieved": q_bytes / (t_query_a / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": q_bytes / (t_query_a / 1e3) / 1e9 / peak, "traffic": traffic,
+                     "traffic_note": traffic_note,
+                     "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                     "algorithmic_bytes_per_call": q_bytes, "call_ms": t_query_a,
+                     "bytes_model": "gather model without values: CSR + local rows once + one "
+                                    "dense row per nonzero + float32 output once"},
+        "e2e": {"value": units_sweep / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        # per side: b (SpMM), M x0, cg_init, then per iteration a query and a
+        # row update; the B side's SpMM^T first permutes c; split rows add
+        # a combine per pass over S
+        "gpu_launches": K * (2 * (3 + 2 * iters) + 1 + (
+            (2 + iters) if plan.info()["split_rows"] else 0) + (
+            (2 + iters) if plan.info()["split_cols"] else 0)),
         "clocks": clk,
     }
     if not args.no_cpu_baseline:
@@ -844,7 +951,7 @@ def run_gat(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
 
     def timed(fn, reps):
-        for _ in range(3):
+        for _ in range(max(3, args.warmup)):
             fn()
         torch.cuda.synchronize()
         a0 = torch.cuda.Event(enable_timing=True); a1 = torch.cuda.Event(enable_timing=True)
@@ -859,32 +966,88 @@ def run_gat(args, rank, world, local_rank):
     clocks.start()
     attn_ms = timed(lambda: fmm.gat_forward(plan, heads, None, f, g, Hp, 0.2, out=out), args.steps)
     clk = clocks.stop()
+    # end to end: H, f and g from pinned host memory, the output read back
+    Hh, fh, gh = Hp.cpu().pin_memory(), f.cpu().pin_memory(), g.cpu().pin_memory()
+    out_h = torch.empty(nv, r).pin_memory()
+
+    def e2e_step():
+        Hp.copy_(Hh, non_blocking=True)
+        f.copy_(fh, non_blocking=True)
+        g.copy_(gh, non_blocking=True)
+        fmm.gat_forward(plan, heads, None, f, g, Hp, 0.2, out=out)
+        out_h.copy_(out, non_blocking=True)
+
+    e2e_ms = timed(e2e_step, max(3, args.steps // 2))
+    h2d = Hh.numel() * Hh.element_size() + (fh.numel() + gh.numel()) * 4
+    d2h = out_h.numel() * 4
     layer_ms = timed(lambda: gat.gat_layer(plan, X, W, a_l, a_r, heads), max(3, args.steps // 4))
     nnz = ci.numel()
     e = 4 if tdt == torch.float32 else 2
     model = 4 * (nv + 1) + 4 * nnz + nnz * (r * e + 4 * heads) + nv * (4 * heads + 4 * r)
     peak, peak_kind = load_peaks()
+    wname = (f"GAT forward, R-MAT 2^{scale} (a,b,c,d)=(.57,.19,.19,.05), avg degree 16, "
+             f"{heads} heads x {rh}")
+    traffic, traffic_note = read_traffic(wname, "fmm_gat_forward", "bf16" if e == 2 else "f32")
+    info = plan.info()
     line = {
         "metric": METRIC, "value": nnz * r / (attn_ms / 1e3), "unit": UNIT, "n_gpus": 1,
-        "steps": args.steps, "warmup": 3, "ms_per_step": attn_ms, "higher_is_better": True,
+        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": attn_ms,
+        "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" + (" (bf16 H)" if tdt == torch.bfloat16 else ""), "data": "synthetic",
-        "config": {"workload": f"GAT forward, R-MAT 2^{scale} (a,b,c,d)=(.57,.19,.19,.05), avg "
-                               f"degree 16, {heads} heads x {rh}", "nnz": nnz, "r": r,
+        "config": {"workload": wname, "nnz": nnz, "r": r, "slope": 0.2,
+                   "l2": "not flushed: H is larger than L2",
                    "step": "fmm_gat_forward (scores, row softmax, aggregation); units = nnz*r"},
         "roofline": {"bound": "hbm", "kernel": "gat_kernel", "achieved": model / (attn_ms / 1e3) / 1e9,
                      "peak": peak, "unit": "GB/s",
-                     "frac": model / (attn_ms / 1e3) / 1e9 / peak, "traffic": None,
+                     "frac": model / (attn_ms / 1e3) / 1e9 / peak, "traffic": traffic,
+                     "dram_frac": None if traffic is None else traffic / (attn_ms / 1e3) / 1e9 / peak,
+                     "traffic_note": traffic_note,
                      "peak_kind": f"{peak_kind} copy bandwidth",
                      "bytes_model": "CSR + one H row and the head scores g_j per nonzero + f_i "
                                     "and the output row per row"},
         "gat": {"attention_ms": attn_ms, "layer_ms": layer_ms,
                 "layer": "X W (torch.matmul) + projections + attention"},
-        "gpu_launches": args.steps, "clocks": clk,
+        "e2e": {"value": nnz * r / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "gpu_launches": args.steps * (1 + (1 if info["split_rows"] else 0)), "clocks": clk,
     }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = gat_oracle_sample(rp, ci, f, g, Hp, heads, r, args.cpu_seconds)
     print(json.dumps(line), flush=True)
     plan.close()
     return 0
+
+
+def gat_oracle_sample(rp, ci, f, g, Hp, heads, r, seconds):
+    """The FP64 oracle's attention forward on the first rows of the graph
+    (columns remapped to the ones they touch), sized to about `seconds`."""
+    import oracle
+    rp_h = rp.cpu().numpy().astype(np.int64)
+    ci_h = ci.cpu().numpy()
+    f_h = f.double().cpu().numpy()
+    g_h = g.double().cpu().numpy()
+
+    def run(rows):
+        nz = int(rp_h[rows])
+        cols, cmap = np.unique(ci_h[:nz], return_inverse=True)
+        H = Hp[torch_index(cols, Hp.device)].double().cpu().numpy()
+        t0 = time.perf_counter()
+        oracle.gat(rp_h[:rows + 1], cmap, None, f_h[:rows], g_h[cols], H, heads, 0.2)
+        return time.perf_counter() - t0, nz
+
+    rows = min(len(rp_h) - 1, 4096)
+    t, nz = run(rows)
+    rows = int(min(len(rp_h) - 1, max(rows, rows * seconds / max(t, 1e-6))))
+    t, nz = run(rows)
+    return {"value": nz * r / t, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"first {rows} rows ({nz} nnz) of the graph, columns remapped to the ones "
+                      f"they touch; attention forward in FP64 (oracle/fmm_oracle.c)"}
+
+
+def torch_index(idx, device):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(idx, dtype=np.int64)).to(device)
 
 
 def main():
@@ -906,6 +1069,8 @@ def main():
     ap.add_argument("--scale", type=float, default=1.0, help="row-count scale (1 = full)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-library", action="store_true",
+                    help="skip the cuSPARSE (torch.sparse) comparison")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

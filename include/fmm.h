@@ -97,7 +97,9 @@ typedef struct fmm_plan_options {
                                  nonzeros than this are split into chunks of
                                  this many nonzeros whose partial rows are
                                  summed in a fixed order; 0 = default:
-                                 nnz / 16384 clamped to [256, 8192]          */
+                                 nnz / (4 x the teams of lanes that run at
+                                 once for the kernel variant), clamped to
+                                 [256, 8192]                                  */
     int32_t variant;          /* kernel variant of the vectorised row passes:
                                  0 = chosen by the plan; else V*100 + N*10 + U
                                  with V = vectors per lane (as a multiple of

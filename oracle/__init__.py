@@ -80,8 +80,16 @@ def _load():
             fn = getattr(lib, name)
             fn.argtypes = args
             fn.restype = ctypes.c_int
+        lib.oracle_threads.argtypes = [ctypes.c_int]
+        lib.oracle_threads.restype = ctypes.c_int
         _lib = lib
         return lib
+
+
+def threads(n: int = 0) -> int:
+    """Threads of the oracle's parallel row loops: sets the count when
+    n > 0; returns the count in effect."""
+    return int(_load().oracle_threads(int(n)))
 
 
 def _i64(x):

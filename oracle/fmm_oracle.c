@@ -414,3 +414,20 @@ int oracle_gat(int64_t m, int64_t n, int64_t heads, int64_t rh, const int64_t *r
     }
     return 0;
 }
+
+/* Thread count of the row loops (timing of the CPU baseline only): sets it
+ * when n > 0, and returns the number of threads a parallel row loop uses. */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+int oracle_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0)
+        omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}

@@ -121,6 +121,9 @@ int encode_variant(const KernelVariant &v);
 // Default kernel variant of a pass over rows of width r (dtype, average
 // nonzeros per row).
 KernelVariant default_variant(int32_t r, int32_t dtype, double avg_nnz);
+// Default split size of long rows for a pattern of nnz nonzeros and rows of
+// width r run with variant v.
+int32_t default_split_nnz(int64_t nnz, int32_t r, int32_t dtype, const KernelVariant &v);
 
 // Plan construction and error reporting (fmm_plan.cu).
 int check_csr_args(const fmm_csr *S);

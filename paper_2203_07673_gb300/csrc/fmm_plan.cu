@@ -485,13 +485,12 @@ int create_plan(const fmm_csr *S, int32_t r, int32_t dtype, const fmm_plan_optio
     fmm_plan *p = new fmm_plan();
     p->m = S->m; p->n = S->n; p->nnz = S->nnz; p->r = r; p->dtype = dtype;
     p->flags = opt ? opt->flags : 0u;
-    // A row is split when one team would still be busy with it after the
-    // other teams finished everything else: with rows longest-first, that is
-    // a row of more than about nnz / (2 x concurrent teams) nonzeros.  About
-    // 16K teams run at once on 152 SMs, hence nnz / 16384, within [256, 8192].
-    p->split_nnz = (int32_t)std::min<int64_t>(8192, std::max<int64_t>(256, S->nnz / 16384));
-    if (opt && opt->split_nnz > 0) p->split_nnz = opt->split_nnz;
     if (opt) p->variant = opt->variant;
+    const KernelVariant row_variant =
+        p->variant ? decode_variant(p->variant)
+                   : default_variant(r, dtype, S->m ? (double)S->nnz / S->m : 0.0);
+    p->split_nnz = default_split_nnz(S->nnz, r, dtype, row_variant);
+    if (opt && opt->split_nnz > 0) p->split_nnz = opt->split_nnz;
     cudaGetDevice(&p->device);
     Temps tmp;
     const int64_t N = std::max<int64_t>({(int64_t)S->m, (int64_t)S->n, S->nnz, 1});
@@ -517,8 +516,7 @@ int create_plan(const fmm_csr *S, int32_t r, int32_t dtype, const fmm_plan_optio
     if (rc) return fail(rc);
     p->rows.col_idx = S->col_idx;
     p->rows.perm = nullptr;
-    p->rows.variant = p->variant ? decode_variant(p->variant)
-                                 : default_variant(r, dtype, S->m ? (double)S->nnz / S->m : 0.0);
+    p->rows.variant = row_variant;
 
     if (!(p->flags & FMM_PLAN_NO_TRANSPOSE)) {
         p->has_t = true;
@@ -581,6 +579,32 @@ KernelVariant default_variant(int32_t r, int32_t dtype, double avg_nnz)
     // vectors per lane make 8 elements
     v.vpl_mult = (dtype == FMM_F32 && vecs <= 32) ? 2 : 1;
     return v;
+}
+
+// Split size of long rows.  Chunks are scheduled first, and one team works
+// through a chunk U*NG nonzeros per dependent step, while all concurrent
+// teams share the rest of the pass; a chunk must end well before the pass
+// does, so it holds at most nnz / (4 x concurrent teams) nonzeros.  Teams
+// at once: SMs x 32 resident warps x teams per warp (32 / lanes per team of
+// the variant; rows of the generic kernel take a warp).  Within [256, 8192].
+// (On R-MAT 2^22 with BF16 rows of r = 64 this gives about 840; chunks of
+// 3982 made that forward pass 15 % slower than chunks of 1024.)
+int32_t default_split_nnz(int64_t nnz, int32_t r, int32_t dtype, const KernelVariant &v)
+{
+    const int e = dtype == FMM_BF16 ? 2 : 4;
+    int lanes = 32;
+    if (fast_r(r)) {
+        const int vecs = r * e / 16;
+        const int vpl = (vecs > 32 ? vecs / 32 : 1) * v.vpl_mult;
+        lanes = std::min(32, std::max(1, vecs / std::max(1, vpl)) * std::max(1, v.ng));
+    }
+    int sms = 0, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms <= 0)
+        sms = 152;
+    const int64_t teams = (int64_t)sms * 32 * (32 / lanes);
+    return (int32_t)std::min<int64_t>(8192, std::max<int64_t>(256, nnz / (4 * teams)));
 }
 
 // dst[q] = src[perm[q]].  Each block covers 1024 consecutive q, each thread
