@@ -115,3 +115,26 @@ def test_registered_values_skip_the_permutation():
                             np.ones((S.m, r)), S.n)
     assert relF(dB.double().cpu().numpy(), e[1]) <= 1e-5
     plan.set_values(None)
+
+
+@pytest.mark.parametrize("offset", [4, 8], ids=["16B", "32B"])
+def test_gat_h_alignment(offset):
+    """float32 H rows are loaded 32 bytes per lane: H that is only 16-byte
+    aligned takes the generic kernel; both must match the oracle."""
+    from paper_2203_07673_gb300 import fmm
+    S, rng = _graph(21, m=400)
+    heads, rh = 4, 32
+    r = heads * rh
+    H = (rng.standard_normal((S.n, r)) * 0.5).astype(np.float32)
+    f = rng.standard_normal((S.m, heads)).astype(np.float32)
+    g = rng.standard_normal((S.n, heads)).astype(np.float32)
+    buf = torch.zeros(S.n * r + 8, device="cuda")
+    buf[offset:offset + S.n * r] = torch.from_numpy(H).reshape(-1).cuda()
+    Ht = buf[offset:offset + S.n * r].view(S.n, r)
+    assert (Ht.data_ptr() % 32 == 0) == (offset == 8)
+    rp, ci = torch.from_numpy(S.row_ptr).cuda(), torch.from_numpy(S.col_idx).cuda()
+    plan = fmm.Plan(rp, ci, S.n, r, split_nnz=256)
+    out = fmm.gat_forward(plan, heads, None, torch.from_numpy(f).cuda(),
+                          torch.from_numpy(g).cuda(), Ht, 0.2)
+    ref = oracle.gat(S.row_ptr, S.col_idx, None, f, g, H.astype(np.float64), heads, 0.2)
+    assert relF(out.double().cpu().numpy(), ref) <= 1e-5
