@@ -342,6 +342,65 @@ def run_reference(args, rank, world):
     return 0
 
 
+def serial_e2e(compute, host_in, slot_in, host_out, slot_out):
+    """One end-to-end step on the current stream: uploads, compute, read-backs."""
+    for h, d in zip(host_in, slot_in[0]):
+        if h is not None:
+            d.copy_(h, non_blocking=True)
+    compute(0)
+    for h, d in zip(host_out, slot_out[0]):
+        h.copy_(d, non_blocking=True)
+
+
+def pipelined_e2e(compute, host_in, slot_in, host_out, slot_out, reps, warmup, barrier):
+    """Milliseconds per end-to-end step with double buffering: step i uploads
+    its inputs into slot i % 2 on an upload stream, computes on the current
+    stream and reads its outputs back on a read-back stream; a slot is
+    reused only after its previous step's compute and read-back finished.
+    Every step moves all its inputs and outputs inside the timed region."""
+    import torch
+    main = torch.cuda.current_stream()
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    ev = lambda: torch.cuda.Event()  # noqa: E731
+    in_ready, done, out_free = [ev(), ev()], [ev(), ev()], [ev(), ev()]
+    used = [False, False]
+
+    def step(i):
+        slot = i % 2
+        if used[slot]:
+            s_in.wait_event(done[slot])
+        with torch.cuda.stream(s_in):
+            for h, d in zip(host_in, slot_in[slot]):
+                if h is not None:
+                    d.copy_(h, non_blocking=True)
+            in_ready[slot].record(s_in)
+        main.wait_event(in_ready[slot])
+        if used[slot]:
+            main.wait_event(out_free[slot])
+        compute(slot)
+        done[slot].record(main)
+        s_out.wait_event(done[slot])
+        with torch.cuda.stream(s_out):
+            for h, d in zip(host_out, slot_out[slot]):
+                h.copy_(d, non_blocking=True)
+            out_free[slot].record(s_out)
+        used[slot] = True
+
+    for i in range(warmup):
+        step(i)
+    barrier()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(main)
+    s_in.wait_stream(main)
+    s_out.wait_stream(main)
+    for i in range(warmup, warmup + reps):
+        step(i)
+    main.wait_stream(s_out)
+    t1.record(main)
+    barrier()
+    return t0.elapsed_time(t1) / reps
+
+
 def cusparse_forward(rp, ci, vals, A, B, S, r, fused_out, timed):
     """FusedMMA by library calls for comparison: the cuSPARSE SDDMM and SpMM
     behind torch.sparse (sampled_addmm, then the values scaled by s, then a
@@ -504,22 +563,34 @@ def run_fmm(args, rank, world, local_rank):
     dA_h = None if G is None else torch.empty(S.m, r).pin_memory()
     ds_h = None if G is None else torch.empty(S.nnz).pin_memory()
 
-    def e2e_step():
-        A.copy_(A_h, non_blocking=True)
-        B.copy_(B_h, non_blocking=True)
-        if vals is not None:
-            vals.copy_(vals_h, non_blocking=True)
-        if G is not None:
-            G.copy_(G_h, non_blocking=True)
-        for f in fns:
-            f()
-        out_h.copy_(out, non_blocking=True)
-        second_h.copy_(dB if k == 3 else out_t, non_blocking=True)
-        if G is not None:
-            dA_h.copy_(dA, non_blocking=True)
-            ds_h.copy_(ds, non_blocking=True)
+    # two device copies of every input and output: step i uses slot i % 2,
+    # so its uploads overlap step i - 1's compute and read-back
+    def second(t):
+        return None if t is None else torch.empty_like(t)
 
-    e2e_ms = timed(e2e_step, max(3, min(K, 30)))
+    slot_in = [[A, B, vals, G], [second(A), second(B), second(vals), second(G)]]
+    outs0 = [out, dB if k == 3 else out_t] + ([dA, ds] if k == 3 else [])
+    slot_out = [outs0, [second(t) for t in outs0]]
+    host_in = [A_h, B_h, vals_h, G_h]
+    host_out = [out_h, second_h] + ([dA_h, ds_h] if k == 3 else [])
+
+    def compute(slot):
+        Ab, Bb, vb, Gb = slot_in[slot]
+        o = slot_out[slot]
+        fmm.fusedmm(plan, vb, Ab, Bb, out=o[0])
+        if k == 3:
+            rc = lib.fmm_fusedmm_bwd(plan.handle, vb.data_ptr(), Ab.data_ptr(), Bb.data_ptr(),
+                                     Gb.data_ptr(), o[2].data_ptr(), o[1].data_ptr(),
+                                     o[3].data_ptr(), torch.cuda.current_stream().cuda_stream)
+            fmm._check(rc, "fmm_fusedmm_bwd")
+        else:
+            fmm.fusedmm_t(plan, vb, Ab, Bb, out=o[1])
+
+    e2e_reps = max(3, min(K, 30))
+    e2e_ms = pipelined_e2e(compute, host_in, slot_in, host_out, slot_out, e2e_reps,
+                           max(3, min(args.warmup, 5)), barrier)
+    e2e_serial_ms = timed(lambda: serial_e2e(compute, host_in, slot_in, host_out, slot_out),
+                          max(3, min(K, 10)))
     library_fwd = None if args.no_library else cusparse_forward(
         rp, ci, vals, A, B, S, r, out, lambda fn: timed(fn, max(3, min(K, 20))))
     unfused_ms, fused_ms, e2e_ms = reduce_max([unfused_ms, fused_ms, e2e_ms], dev, world)
@@ -570,7 +641,10 @@ def run_fmm(args, rank, world, local_rank):
             "speedup": unfused_ms / fused_ms,
             "unfused": "fmm_sddmm + fmm_spmm + fmm_sddmm + fmm_spmm_t"},
         "e2e": {"value": units_step * world / (e2e_ms / 1e3), "unit": UNIT,
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+                "pipeline": "two buffer sets: uploads on one stream, read-backs on another, "
+                            "overlapping the neighbouring steps' compute",
+                "serial_ms_per_step": e2e_serial_ms},
         "gpu_launches": K * sum(launches[name] for name, _ in calls),
         "clocks": clk,
         "plan": {kk: info[kk] for kk in ("max_row_nnz", "max_col_nnz", "split_rows",
