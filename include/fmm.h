@@ -108,7 +108,11 @@ typedef struct fmm_plan_options {
                                  per group per batch; one of 112, 114, 118,
                                  122, 124, 212, 214, 221, 222, 224, 441, 442
                                  (a code that does not fit the row width
-                                 falls back to 118)                          */
+                                 falls back to 118); or 1000 + D*10 + V
+                                 (1041, 1042, 1081, 1082): FusedMM, SDDMM
+                                 and SpMM stage the next D - 1 gathered rows
+                                 of each row in shared memory (cp.async),
+                                 the backward passes use V*100 + 12          */
 } fmm_plan_options;
 
 typedef struct fmm_plan fmm_plan;   /* opaque */

@@ -20,7 +20,7 @@ import torch
 
 from . import fmm
 
-ALL_CODES = (112, 114, 118, 122, 124, 212, 214, 221, 222, 224, 441, 442)
+ALL_CODES = (112, 114, 118, 122, 124, 212, 214, 221, 222, 224, 441, 442, 1041, 1042, 1081, 1082)
 BATCH_CODES = (112, 114, 122, 212, 214, 221)
 
 

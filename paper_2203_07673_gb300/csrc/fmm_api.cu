@@ -13,8 +13,11 @@ static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 
 // Variant codes: vectors-per-lane multiple * 100 + groups per team * 10 +
 // nonzeros per group per batch (the combinations instantiated in
 // fmm_rows.cuh; a combination that does not fit a row shape falls back to
-// the shape's default).
-static const int kVariantCodes[] = {114, 118, 222, 224, 441, 442, 214, 124, 112, 122, 212, 221};
+// the shape's default); 1000 + ring depth * 10 + vectors-per-lane multiple
+// for the staged pass (fmm_staged.cuh), whose backward roles run the team
+// kernel with 2 nonzeros per batch.
+static const int kVariantCodes[] = {114, 118, 222, 224, 441, 442, 214, 124, 112, 122, 212, 221,
+                                    1041, 1042, 1081, 1082};
 
 bool variant_known(int code)
 {
@@ -26,19 +29,35 @@ bool variant_known(int code)
 KernelVariant decode_variant(int code)
 {
     KernelVariant v;
+    if (code >= 1000) {
+        v.stages = (code / 10) % 100;
+        v.vpl_mult = code % 10;
+        v.ng = 1;
+        v.u = 2;
+        return v;
+    }
     v.vpl_mult = code / 100;
     v.ng = (code / 10) % 10;
     v.u = code % 10;
     return v;
 }
 
-int encode_variant(const KernelVariant &v) { return v.vpl_mult * 100 + v.ng * 10 + v.u; }
+int encode_variant(const KernelVariant &v)
+{
+    if (v.stages > 0)
+        return 1000 + v.stages * 10 + v.vpl_mult;
+    return v.vpl_mult * 100 + v.ng * 10 + v.u;
+}
 
 cudaError_t launch_pass(int mode, int dtype, const KernelVariant &v, const PassArgs &a,
                         cudaStream_t st)
 {
     const bool vec = fast_r(a.r) && aligned16(a.L) && aligned16(a.Y) && aligned16(a.H) &&
                      aligned16(a.out) && aligned16(a.partials);
+    if (v.stages > 0 && vec && (mode == M_FUSED || mode == M_SDDMM || mode == M_SPMM)) {
+        return dtype == FMM_BF16 ? launch_staged_bf16(mode, v.vpl_mult, v.stages, a, st)
+                                 : launch_staged_f32(mode, v.vpl_mult, v.stages, a, st);
+    }
     if (dtype == FMM_BF16)
         return launch_pass_bf16(mode, v.vpl_mult, v.ng, v.u, vec, a, st);
     return launch_pass_f32(mode, v.vpl_mult, v.ng, v.u, vec, a, st);

@@ -15,6 +15,7 @@ namespace fmm {
 // per batch.
 struct KernelVariant {
     int vpl_mult = 1, ng = 1, u = 8;
+    int stages = 0;   // > 0: the staged pass (fmm_staged.cuh) with this ring depth
 };
 
 // One side of a plan: the CSR that a row pass walks (S itself, or S^T with a
@@ -107,6 +108,12 @@ cudaError_t launch_pass_f32(int mode, int vpl_mult, int ng, int u, bool vec, con
                             cudaStream_t st);
 cudaError_t launch_pass_bf16(int mode, int vpl_mult, int ng, int u, bool vec, const PassArgs &a,
                              cudaStream_t st);
+// Staged forward-role passes (fmm_staged.cuh): FusedMM, SDDMM and SpMM with a
+// cp.async ring of `stages` gathered rows per team; vector path only.
+cudaError_t launch_staged_f32(int mode, int vpl_mult, int stages, const PassArgs &a,
+                              cudaStream_t st);
+cudaError_t launch_staged_bf16(int mode, int vpl_mult, int stages, const PassArgs &a,
+                               cudaStream_t st);
 // dst[q] = src[perm[q]] for q < nnz (values of S into the order of S^T).
 cudaError_t launch_permute(const float *src, const int32_t *perm, float *dst, int64_t nnz,
                            cudaStream_t st);

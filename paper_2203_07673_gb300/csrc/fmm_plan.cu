@@ -578,6 +578,13 @@ KernelVariant default_variant(int32_t r, int32_t dtype, double avg_nnz)
     // float32 rows of at most 32 vectors hold 4 elements per vector: two
     // vectors per lane make 8 elements
     v.vpl_mult = (dtype == FMM_F32 && vecs <= 32) ? 2 : 1;
+    // float32 rows of r = 128 (512 bytes): the staged pass with a ring of 4
+    // gathered rows per team, 3-4 % faster on Erdos-Renyi rows at the DRAM
+    // roofline (it needs no register spill); where gathers mostly hit L2 the
+    // extra trip through shared memory costs more than the deeper ring
+    // gains, and the team kernel stays
+    if (dtype == FMM_F32 && r == 128)
+        v.stages = 4;
     return v;
 }
 

@@ -100,7 +100,8 @@ def test_parity_all_ops(kind, r, dtype):
     run_all(S, opts, r, dtype, seed=r, check_bf16_vs_f32=(dtype == torch.bfloat16))
 
 
-@pytest.mark.parametrize("variant", [114, 118, 222, 224, 441, 442, 214, 124, 112, 122, 212, 221])
+@pytest.mark.parametrize("variant", [114, 118, 222, 224, 441, 442, 214, 124, 112, 122, 212, 221,
+                                     1041, 1042, 1081, 1082])
 @pytest.mark.parametrize("split_nnz", [16, 0])
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16], ids=["f32", "bf16"])
 @pytest.mark.parametrize("r", [32, 128, 256])
@@ -303,3 +304,30 @@ def test_value_permutation_large_unaligned(offset):
     plan.set_values(vt)
     assert torch.equal(fmm.fusedmm_t(plan, vt, At, Bt), got)
     plan.set_values(None)
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16], ids=["f32", "bf16"])
+@pytest.mark.parametrize("r", [32, 64, 128, 256])
+@pytest.mark.parametrize("staged,team", [(1041, 112), (1081, 112), (1042, 212), (1082, 212)])
+def test_staged_pass_equals_team_pass_bitwise(r, dtype, staged, team):
+    """The staged pass (gathered rows in flight in shared memory) adds the
+    same products in the same order as the team kernel with one group and
+    two nonzeros per batch: FusedMM, FusedMMB, SDDMM and SpMM agree bit for
+    bit, with long rows split and empty rows present."""
+    from paper_2203_07673_gb300 import fmm
+    S, _ = pattern("hubs", 11)
+    rng = np.random.default_rng(r)
+    vals = rng.uniform(0.0, 1.0, S.nnz).astype(np.float32)
+    A = rng.standard_normal((S.m, r)).astype(np.float32)
+    B = rng.standard_normal((S.n, r)).astype(np.float32)
+    v_in = torch.from_numpy(rng.standard_normal(S.nnz).astype(np.float32)).cuda()
+    rp, ci, vt, At, Bt = upload(S, vals, A, B, dtype)
+    out = {}
+    for code in (staged, team):
+        plan = fmm.Plan(rp, ci, S.n, r, dtype, split_nnz=48, variant=code)
+        out[code] = (fmm.fusedmm(plan, vt, At, Bt), fmm.fusedmm_t(plan, vt, At, Bt),
+                     fmm.sddmm(plan, vt, At, Bt), fmm.spmm(plan, v_in, Bt),
+                     fmm.spmm_t(plan, v_in, At), fmm.fusedmm(plan, None, At, Bt))
+        plan.close()
+    for x, y in zip(out[staged], out[team]):
+        assert torch.equal(x, y)
