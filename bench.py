@@ -195,10 +195,15 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_workload(k: int, scale: float):
+def make_workload(k: int, scale: float, bf16: bool = False):
+    """Workload k; bf16 runs the FP32 workloads (2, 4) with A and B rounded
+    to bfloat16 (the BF16 case of the Zipf-row configuration)."""
     from paper_2203_07673_gb300 import workloads as wl
     w = wl.workload(k, scale_rows=scale)
     w["k"] = k
+    if bf16 and w["dtype"] == "f32":
+        w["dtype"] = "bf16"
+        w["name"] = w["name"] + " [BF16 A,B]"
     return w
 
 
@@ -318,7 +323,7 @@ def run_reference(args, rank, world):
         return 0
     if args.workload == 5:
         return run_reference_batched(args)
-    w = make_workload(args.workload, args.scale)
+    w = make_workload(args.workload, args.scale, args.bf16)
     # calibrate one step to about 1 s of CPU work, then time W + K steps
     _, _, _, rows = oracle_sample(w, 1.0)
     for _ in range(args.warmup):
@@ -451,7 +456,7 @@ def run_fmm(args, rank, world, local_rank):
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    w = make_workload(args.workload, args.scale)
+    w = make_workload(args.workload, args.scale, args.bf16)
     S, r, k = w["S"], w["r"], args.workload
     tdt = torch.float32 if w["dtype"] == "f32" else torch.bfloat16
     e = 4 if w["dtype"] == "f32" else 2
@@ -1141,6 +1146,8 @@ def main():
     ap.add_argument("--heads", type=int, default=4)
     ap.add_argument("--head-dim", type=int, default=32)
     ap.add_argument("--gat-bf16", action="store_true")
+    ap.add_argument("--bf16", action="store_true",
+                    help="workloads 2 and 4 with BF16 A and B (FP32 accumulation)")
     ap.add_argument("--scale", type=float, default=1.0, help="row-count scale (1 = full)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
