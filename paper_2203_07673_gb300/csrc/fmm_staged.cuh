@@ -20,6 +20,8 @@
 // with one group per row.
 #pragma once
 
+#include <atomic>
+
 #include "fmm_rows.cuh"
 
 namespace fmm {
@@ -215,13 +217,22 @@ cudaError_t launch_staged(const PassArgs &a, cudaStream_t st)
 {
     constexpr int G = TeamShape<T, R, VPL, 1>::G;
     constexpr size_t smem = (size_t)D * VPL * 256 * 16;
-    static bool attr_set = false;   // per instantiation, set before first use
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(staged_pass_kernel<MODE, T, R, VPL, D>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if constexpr (smem > 48 * 1024) {
+        // more than the default dynamic shared memory: raise the kernel's
+        // limit once per device (a bit per device of the first 64)
+        static std::atomic<unsigned long long> done{0};
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
         if (e != cudaSuccess)
             return e;
-        attr_set = true;
+        const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+        if (!bit || !(done.load() & bit)) {
+            e = cudaFuncSetAttribute(staged_pass_kernel<MODE, T, R, VPL, D>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess)
+                return e;
+            done.fetch_or(bit);
+        }
     }
     const long long total = (long long)a.n_chunks + a.n_light;
     const long long blocks = (total * G + 255) / 256;
