@@ -123,3 +123,36 @@ def test_rmat_2p22_r64_bf16_forward_backward():
     mag = oracle.fusedmm_grad(srp, sci, None, np.abs(A_r), np.abs(B_c), np.abs(G_r), len(cols))
     cdeg = int(np.bincount(S.col_idx, minlength=S.n).max())
     _cmp("dB cols", dB[t(cols)].double().cpu().numpy(), ref[1], mag[1], 2 * r + cdeg + 4)
+
+
+def test_er_4096_r32_f32_every_output_element():
+    """The small configuration (ER 4096 x 4096, 32 distinct columns per row,
+    r = 32, FP32, s ~ U(0,1)) at its exact size: every element of FusedMMA,
+    FusedMMB, SDDMM, the unfused SDDMM -> SpMM chain and both gradients
+    against the oracle."""
+    from paper_2203_07673_gb300 import fmm
+    from parity_utils import absolute, assert_close, deg_max, oracle_all
+    w = wl.workload(1)
+    S, r = w["S"], w["r"]
+    rp, ci, vt, At, Bt = _upload(w, torch.float32)
+    plan = fmm.Plan(rp, ci, S.n, r, torch.float32)   # as bench.py would
+    rng = np.random.default_rng(9)
+    G = rng.standard_normal((S.m, r)).astype(np.float32)
+    Gn = rng.standard_normal((S.n, r)).astype(np.float32)
+    Gt, Gnt = torch.from_numpy(G).cuda(), torch.from_numpy(Gn).cuda()
+    v = fmm.sddmm(plan, vt, At, Bt)
+    got = dict(fusedmm=fmm.fusedmm(plan, vt, At, Bt), fusedmm_t=fmm.fusedmm_t(plan, vt, At, Bt),
+               sddmm=v, unfused=fmm.spmm(plan, v, Bt),
+               bwd=fmm.fusedmm_bwd(plan, vt, At, Bt, Gt),
+               t_bwd=fmm.fusedmm_t_bwd(plan, vt, At, Bt, Gnt))
+    s64, A64, B64 = w["vals"].astype(np.float64), w["A"].astype(np.float64), w["B"].astype(np.float64)
+    ref = oracle_all(S, s64, A64, B64, G, Gn)
+    mag = oracle_all(S, absolute(s64), np.abs(A64), np.abs(B64), np.abs(G), np.abs(Gn))
+    dm = deg_max(S)
+    for k in ("fusedmm", "fusedmm_t", "sddmm"):
+        assert_close(k, got[k], ref[k], mag[k], r, dm)
+    assert_close("unfused", got["unfused"], ref["fusedmm"], mag["fusedmm"], r + 1, dm)
+    for k in ("bwd", "t_bwd"):
+        for t, name in enumerate(("dA", "dB", "ds")):
+            assert_close(f"{k}.{name}", got[k][t], ref[k][t], mag[k][t], 2 * r, dm)
+    plan.close()

@@ -331,3 +331,45 @@ def test_staged_pass_equals_team_pass_bitwise(r, dtype, staged, team):
         plan.close()
     for x, y in zip(out[staged], out[team]):
         assert torch.equal(x, y)
+
+
+def test_rows_without_nonzeros_are_zeroed():
+    """Outputs are overwritten, rows without nonzeros included: outputs filled
+    with NaN beforehand must come back with exact zeros on those rows
+    (FusedMM, FusedMMB, SpMM, both gradients, GAT, team and staged passes,
+    vector and generic paths), and match the oracle elsewhere."""
+    from paper_2203_07673_gb300 import fmm
+    S = wl.random_csr(900, 1400, np.random.default_rng(5), mean_deg=5, empty_frac=0.2,
+                      dup_frac=0.1, unsorted=True)
+    deg, cdeg = S.degrees(), np.bincount(S.col_idx, minlength=S.n)
+    assert (deg == 0).sum() > 50 and (cdeg == 0).sum() > 20
+    rng = np.random.default_rng(2)
+    for r, code in ((32, 0), (128, 0), (64, 1082), (24, 0)):
+        A = rng.standard_normal((S.m, r)).astype(np.float32)
+        B = rng.standard_normal((S.n, r)).astype(np.float32)
+        vals = rng.uniform(0, 1, S.nnz).astype(np.float32)
+        rp, ci, vt, At, Bt = upload(S, vals, A, B)
+        plan = fmm.Plan(rp, ci, S.n, r, variant=code)
+        nan = lambda *shape: torch.full(shape, float("nan"), device="cuda")  # noqa: E731
+        out, out_t = nan(S.m, r), nan(S.n, r)
+        fmm.fusedmm(plan, vt, At, Bt, out=out)
+        fmm.fusedmm_t(plan, vt, At, Bt, out=out_t)
+        sp = fmm.spmm(plan, vt, Bt, out=nan(S.m, r))
+        G = torch.randn(S.m, r, device="cuda")
+        dA, dB, ds = fmm.fusedmm_bwd(plan, vt, At, Bt, G)
+        for name, t, empty in (("fusedmm", out, deg == 0), ("fusedmm_t", out_t, cdeg == 0),
+                               ("spmm", sp, deg == 0), ("dA", dA, deg == 0),
+                               ("dB", dB, cdeg == 0)):
+            h = t.cpu().numpy()
+            assert np.all(h[empty] == 0.0), name
+            assert np.all(np.isfinite(h)), name
+        ref = oracle.fusedmm(S.row_ptr, S.col_idx, vals, A, B, S.n)
+        assert relF(out.double().cpu().numpy(), ref) <= 1e-5
+        if r % 8 == 0:
+            heads = 2
+            f = torch.randn(S.m, heads, device="cuda")
+            g = torch.randn(S.n, heads, device="cuda")
+            go = fmm.gat_forward(plan, heads, vt, f, g, Bt, 0.2, out=nan(S.m, r))
+            h = go.cpu().numpy()
+            assert np.all(h[deg == 0] == 0.0) and np.all(np.isfinite(h))
+        plan.close()
