@@ -150,14 +150,20 @@ class ClockSampler:
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
 
+    log_path = None   # --clock-log: keep the raw samples here (else a temporary file)
+
     def __init__(self, device_index: int):
+        import tempfile
         self.proc = None
         self.dev = device_index
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+        self.path = (ClockSampler.log_path + f".rank{device_index}.csv" if ClockSampler.log_path
+                     else os.path.join(tempfile.gettempdir(),
+                                       f"fmm_clocks_{os.getpid()}_rank{device_index}.csv"))
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            if os.path.dirname(self.path):
+                os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
@@ -1151,11 +1157,14 @@ def main():
     ap.add_argument("--scale", type=float, default=1.0, help="row-count scale (1 = full)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clock-log", default=None,
+                    help="keep nvidia-smi's raw clock samples under this path prefix")
     ap.add_argument("--no-library", action="store_true",
                     help="skip the cuSPARSE (torch.sparse) comparison")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    ClockSampler.log_path = args.clock_log
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
