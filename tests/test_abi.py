@@ -101,3 +101,42 @@ def test_missing_library_fails_loudly(monkeypatch, fmm_lib):
     monkeypatch.setattr(fmm_lib, "LIB_PATH", "/nonexistent/libfmm.so")
     with pytest.raises(RuntimeError, match="not built"):
         fmm_lib.lib()
+
+
+def test_header_compiles_as_c_and_links(fmm_lib, tmp_path):
+    """A C11 caller: include/fmm.h compiles as plain C (no C++ or CUDA headers
+    needed), links against libfmm.so, and its host-side checks answer through
+    the C ABI without a GPU."""
+    import shutil
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "caller.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <string.h>
+#include "fmm.h"
+int main(void)
+{
+    fmm_plan *plan = (fmm_plan *)1;
+    fmm_csr csr;
+    memset(&csr, 0, sizeof csr);
+    csr.m = -1; csr.n = 4;
+    if (fmm_plan_create(NULL, 32, FMM_F32, NULL, NULL, &plan) != FMM_EINVAL || plan) return 1;
+    if (fmm_plan_create(&csr, 32, FMM_F32, NULL, NULL, &plan) != FMM_EINVAL) return 2;
+    if (fmm_plan_destroy(NULL) != FMM_OK) return 3;
+    if (fmm_fusedmm(NULL, NULL, NULL, NULL, NULL, NULL) != FMM_EINVAL) return 4;
+    if (fmm_version() <= 0 || !fmm_status_string(FMM_EINVAL)[0]) return 5;
+    printf("%d %s\n", (int)fmm_version(), fmm_status_string(FMM_EOVERFLOW));
+    return 0;
+}
+''')
+    lib_dir = os.path.dirname(fmm_lib.LIB_PATH)
+    exe = tmp_path / "caller"
+    res = subprocess.run([gcc, "-std=c11", "-Wall", "-Werror", "-pedantic",
+                          "-I" + os.path.join(ROOT, "include"),
+                          str(src), "-o", str(exe), f"-L{lib_dir}", "-l:libfmm.so",
+                          f"-Wl,-rpath,{lib_dir}"], capture_output=True, text=True)
+    assert res.returncode == 0, res.stderr
+    run = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert run.returncode == 0, (run.returncode, run.stderr)
