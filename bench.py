@@ -8,8 +8,13 @@ A, B ~ N(0, 1/128).  The metric counts nnz * r per FusedMM call, so one step
 is 2 * nnz * r units.  Beside it the unfused path (SDDMM writes v, SpMM reads
 it) is timed on the same inputs.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload 1..4]
-  python bench.py --impl reference ...   (the FP64 CPU oracle on host cores)
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload 1..5] [--bf16]
+  python bench.py --als | --gat [--gat-bf16]   (ALS sweeps; graph-attention forward)
+  python bench.py --impl reference ...          (the FP64 CPU oracle on host cores)
+
+Workloads: 1 ER 4096^2 (r = 32), 2 ER 2^20 (r = 128, the default), 3 R-MAT
+2^22 forward + backward (BF16), 4 Zipf rows 2^21 x 2^19 (r = 64; --bf16 for
+BF16 A and B), 5 512 uneven matrices in one persistent launch per phase.
 
 Under torchrun each rank runs its own replica (weak scaling: the path has no
 exchange step); value = units of all ranks / max-over-ranks time.
