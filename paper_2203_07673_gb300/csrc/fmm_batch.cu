@@ -154,8 +154,10 @@ int batch_code(int dtype, int mode, int r, const KernelVariant &v)
                                        : batch_supported<float>(mode, r, want));
     if (ok)
         return want;
-    // the default of the width with fewer nonzeros per batch if needed
+    // the default team layout of the width (the batch kernels run the team
+    // pass only), with fewer nonzeros per batch if needed
     KernelVariant d = default_variant(r, dtype, 0.0);
+    d.stages = 0;
     for (int u : {d.u, 2, 1}) {
         d.u = u;
         const int c = encode_variant(d);
