@@ -104,41 +104,65 @@ __global__ void __launch_bounds__(256, 5) gat_kernel(const GatArgs a)
 #pragma unroll
     for (int e = 0; e < 8; ++e) acc[e] = 0.f;
 
-    const int iters = (end - beg + U - 1) / U;
-    const int witers = (int)__reduce_max_sync(0xffffffffu, (unsigned)iters);
-    for (int it = 0; it < witers; ++it) {
-        int jj[U];
-        float sv[U];
+    // The team loads the column indices and values of IB >= 16 consecutive
+    // nonzeros at once (K per lane, coalesced) and hands them to its batches
+    // by shuffles, so the index latency is paid once per IB / U batches.
+    constexpr int K = G >= 16 ? 1 : 16 / G;
+    constexpr int IB = K * G;
+    static_assert(IB % U == 0, "whole batches per index block");
+    const int tbase = lane & ~(G - 1);
+    const int blocks = (end - beg + IB - 1) / IB;
+    const int wblocks = (int)__reduce_max_sync(0xffffffffu, (unsigned)blocks);
+    for (int bk = 0; bk < wblocks; ++bk) {
+        int mj[K];
+        float ms[K];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int p = beg + it * U + u;
-            jj[u] = p < end ? __ldg(a.col_idx + p) : -1;
-            sv[u] = (p < end && a.s) ? __ldg(a.s + p) : 1.f;
+        for (int e = 0; e < K; ++e) {
+            const int p = beg + bk * IB + e * G + lig;
+            mj[e] = p < end ? __ldg(a.col_idx + p) : -1;
+            ms[e] = (p < end && a.s) ? __ldg(a.s + p) : 1.f;
         }
-        float y[U][8], gj[U];
+#pragma unroll 1
+        for (int sub = 0; sub < IB / U; ++sub) {
+            int jj[U];
+            float sv[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if (jj[u] >= 0) {
-                load8(H + (size_t)jj[u] * R + 8 * lig, y[u]);
-                gj[u] = __ldg(g + (size_t)jj[u] * a.heads);
+            for (int u = 0; u < U; ++u) {
+                const int o = sub * U + u;
+                const int e = o / G, src = tbase + o % G;
+                int jv = mj[0];
+                float svv = ms[0];
+#pragma unroll
+                for (int t = 1; t < K; ++t)
+                    if (e == t) { jv = mj[t]; svv = ms[t]; }
+                jj[u] = __shfl_sync(0xffffffffu, jv, src);
+                sv[u] = __shfl_sync(0xffffffffu, svv, src);
             }
-        }
+            float y[U][8], gj[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if (jj[u] < 0)
-                continue;
-            const float e = leaky(sv[u] * (fi + gj[u]), a.slope);
-            const float d = e - mx;                 // +inf for the first nonzero
-            const float x = __expf(-fabsf(d));      // 0 for the first nonzero
-            if (d > 0.f) {
-                l = fmaf(l, x, 1.f);
+            for (int u = 0; u < U; ++u) {
+                if (jj[u] >= 0) {
+                    load8(H + (size_t)jj[u] * R + 8 * lig, y[u]);
+                    gj[u] = __ldg(g + (size_t)jj[u] * a.heads);
+                }
+            }
 #pragma unroll
-                for (int t = 0; t < 8; ++t) acc[t] = fmaf(acc[t], x, y[u][t]);
-                mx = e;
-            } else {
-                l += x;
+            for (int u = 0; u < U; ++u) {
+                if (jj[u] < 0)
+                    continue;
+                const float e = leaky(sv[u] * (fi + gj[u]), a.slope);
+                const float d = e - mx;                 // +inf for the first nonzero
+                const float x = __expf(-fabsf(d));      // 0 for the first nonzero
+                if (d > 0.f) {
+                    l = fmaf(l, x, 1.f);
 #pragma unroll
-                for (int t = 0; t < 8; ++t) acc[t] = fmaf(x, y[u][t], acc[t]);
+                    for (int t = 0; t < 8; ++t) acc[t] = fmaf(acc[t], x, y[u][t]);
+                    mx = e;
+                } else {
+                    l += x;
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) acc[t] = fmaf(x, y[u][t], acc[t]);
+                }
             }
         }
     }
