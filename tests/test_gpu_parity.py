@@ -93,7 +93,7 @@ def run_all(S, opts, r, dtype, seed, check_bf16_vs_f32=False):
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16], ids=["f32", "bf16"])
-@pytest.mark.parametrize("r", [32, 64, 128, 256, 5, 24, 100])
+@pytest.mark.parametrize("r", [32, 64, 128, 256, 5, 24, 100, 520])
 @pytest.mark.parametrize("kind", ["er", "irregular", "hubs"])
 def test_parity_all_ops(kind, r, dtype):
     S, opts = pattern(kind, 1000 + r)
