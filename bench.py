@@ -776,18 +776,39 @@ def run_batched(args, rank, world, local_rank):
         return a0.elapsed_time(a1) / reps
 
     v_bufs = [torch.empty(it["ci"].numel(), device=dev) for it in items]
+    # the per-matrix baselines use plans of their own with the library's
+    # defaults (variant and long-row splitting: the batch's plans split no
+    # rows, which one matrix at a time would leave hub rows on one team)
+    base_plans = [fmm.Plan(it["rp"], it["ci"], it["plan"].n, it["plan"].r, torch.bfloat16)
+                  for it in items]
 
     def per_matrix_fused():
-        for it in items:
-            fmm.fusedmm(it["plan"], it["vals"], it["A"], it["B"], out=it["out"])
+        for it, bp in zip(items, base_plans):
+            fmm.fusedmm(bp, it["vals"], it["A"], it["B"], out=it["out"])
 
     def per_matrix_unfused():
-        for it, v in zip(items, v_bufs):
-            fmm.sddmm(it["plan"], it["vals"], it["A"], it["B"], out=v)
-            fmm.spmm(it["plan"], v, it["B"], out=it["out"])
+        for it, bp, v in zip(items, base_plans, v_bufs):
+            fmm.sddmm(bp, it["vals"], it["A"], it["B"], out=v)
+            fmm.spmm(bp, v, it["B"], out=it["out"])
 
-    loop_fused_ms = timed(per_matrix_fused)
-    loop_unfused_ms = timed(per_matrix_unfused)
+    # the per-matrix baselines replay from CUDA graphs too, so both sides of
+    # the comparison are GPU time (512 launches from Python would measure
+    # the host)
+    def graphed(fn):
+        side_s = torch.cuda.Stream()
+        side_s.wait_stream(stream)
+        with torch.cuda.stream(side_s):
+            fn()
+        stream.wait_stream(side_s)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            fn()
+        return graph
+
+    g_pm_fused, g_pm_unfused = graphed(per_matrix_fused), graphed(per_matrix_unfused)
+    loop_fused_ms = timed(g_pm_fused.replay)
+    loop_unfused_ms = timed(g_pm_unfused.replay)
 
     # end to end: inputs from pinned host memory, outputs back, every step
     host_in = [(it[k].cpu().pin_memory(), it[k]) for it in items for k in ("vals", "A", "B", "G")]
@@ -842,12 +863,15 @@ def run_batched(args, rank, world, local_rank):
                      "per_matrix_unfused_forward_ms": loop_unfused_ms,
                      "batched_forward_ms": fwd_ms,
                      "speedup_vs_per_matrix_fused": loop_fused_ms / fwd_ms,
-                     "speedup_vs_per_matrix_unfused": loop_unfused_ms / fwd_ms},
+                     "speedup_vs_per_matrix_unfused": loop_unfused_ms / fwd_ms,
+                     "per_matrix": "512 fused (1024 unfused) launches replayed from CUDA graphs, "
+                                   "plans with the library defaults (variant, long-row split)"},
         "e2e": {"value": units_step * world / (e2e_ms / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
         "gpu_launches": 2 * K,
         "clocks": clk,
-        "setup": {"generate_s": gen_s, "autotune_s": tune_s, "tuned_groups": len(tuned)},
+        "setup": {"generate_s": gen_s, "autotune_s": tune_s, "tuned_groups": len(tuned),
+                  "tuned_codes": tuned},
     }
     if rank == 0 and not args.no_cpu_baseline:
         import oracle

@@ -260,7 +260,8 @@ int fmm_plan_set_variant(fmm_plan *plan, int32_t variant, int32_t variant_t);
  * over S^T: dB).  Both can be captured in a CUDA graph.  Each item runs the
  * kernel variant its plan selects (fmm_plan_set_variant), if the batch
  * kernels have it for that width and role (codes 112, 114, 122, 212, 214,
- * 221, with at most 48 floats live per lane), else the width's default with
+ * 221, with at most 32 floats live per lane in the forward phase and 48 in
+ * the backward phase), else the width's default with
  * fewer nonzeros per batch.  Results equal the per-item calls with the same variants
  * bit for bit.  Calls on one batch must be ordered (one stream).
  */

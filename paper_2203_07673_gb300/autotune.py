@@ -88,25 +88,62 @@ def tune_plan(plan: fmm.Plan, vals, A, B, G=None, candidates=ALL_CODES, iters=5,
     return {"variant": best_s, "variant_t": best_t, "ms": times_s, "ms_t": times_t}
 
 
-def tune_batch(items, cache_path: str | None = None, candidates=BATCH_CODES, iters=3):
-    """Tunes the plans of batch items (dicts with plan, vals, A, B, G) by
-    signature group; returns {signature: (variant, variant_t)}."""
+def tune_batch(items, cache_path: str | None = None, candidates=BATCH_CODES, iters=3,
+               min_gain=0.01):
+    """Tunes the plans of batch items (dicts with plan, vals, A, B, out and
+    optionally G, dA, dB, ds) in the batch's own setting: one persistent
+    kernel per phase, whose register count is fixed by its heaviest path, so
+    per-plan timings do not carry over.  Items are grouped by row width and
+    dtype; for each group in turn every candidate code is set on that
+    group's plans (the other groups keep their current codes), the batch is
+    rebuilt and its forward + backward timed, and the group keeps the fastest
+    code if it beats the current one by more than min_gain.  Returns
+    {group: code}."""
+    keys = ("plan", "vals", "A", "B", "out", "G", "dA", "dB", "ds")
     cache = {}
     if cache_path and os.path.exists(cache_path):
         with open(cache_path) as fh:
-            cache = {k: tuple(v) for k, v in json.load(fh).items()}
+            cache = {k: int(v) for k, v in json.load(fh).items()}
     groups = {}
     for it in items:
-        groups.setdefault(signature(it["plan"]), []).append(it)
-    for sig, members in groups.items():
-        if sig not in cache:
-            rep = max(members, key=lambda it: it["plan"].nnz)
-            res = tune_plan(rep["plan"], rep.get("vals"), rep["A"], rep["B"], rep.get("G"),
-                            candidates=candidates, iters=iters)
-            cache[sig] = (res["variant"], res["variant_t"])
+        p = it["plan"]
+        groups.setdefault(f"r{p.r}-{'bf16' if p.dtype == torch.bfloat16 else 'f32'}",
+                          []).append(it)
+    backward = all(it.get("G") is not None for it in items)
+
+    def batch_ms():
+        batch = fmm.Batch([{k: it.get(k) for k in keys} for it in items])
+        try:
+            def step():
+                batch.forward()
+                if backward:
+                    batch.backward()
+            return _time(step, iters)
+        finally:
+            batch.close()
+
+    for g, members in groups.items():
+        if g in cache:
+            for it in members:
+                it["plan"].set_variant(cache[g], cache[g])
+    best = batch_ms()
+    for g, members in groups.items():
+        if g in cache:
+            continue
+        current = members[0]["plan"].info()["variant"]
+        choice = current
+        for code in candidates:
+            if code == current:
+                continue
+            for it in members:
+                it["plan"].set_variant(code, code)
+            t = batch_ms()
+            if t < best * (1.0 - min_gain):
+                best, choice = t, code
         for it in members:
-            it["plan"].set_variant(*cache[sig])
+            it["plan"].set_variant(choice, choice)
+        cache[g] = choice
     if cache_path:
         with open(cache_path, "w") as fh:
-            json.dump({k: list(v) for k, v in cache.items()}, fh, indent=1, sort_keys=True)
+            json.dump(cache, fh, indent=1, sort_keys=True)
     return cache

@@ -48,8 +48,10 @@ __device__ __forceinline__ void run_unit(const PassArgs &a, int begin, int count
 
 // The variant codes a batch can run: one kernel holds every (width, code)
 // path, and its register count is the largest path's, so batches take only
-// light variants (at most 48 floats live per lane in the heaviest role) to
-// keep 32 or more warps per SM resident.
+// light variants: at most 32 floats live per lane in the forward phase (64
+// registers, 4 blocks per SM; with 48 it needed 80 and ran 19 % slower on
+// the 512-matrix batch) and 48 in the backward phase, whose pass over S^T
+// holds two gathered rows per nonzero.
 template <int MODE, typename T>
 constexpr bool batch_code_ok(int r, int code)
 {
@@ -60,7 +62,8 @@ constexpr bool batch_code_ok(int r, int code)
     const int g = vecs / V;
     const int E = V * (16 / (int)sizeof(T));
     const int live = E * (UU * (MODE == M_BWD_COL ? 2 : 1) + 2 + (MODE == M_BWD_ROW ? 1 : 0));
-    return g >= 1 && (g & (g - 1)) == 0 && g * N <= 32 && 32 % (g * N) == 0 && live <= 48;
+    return g >= 1 && (g & (g - 1)) == 0 && g * N <= 32 && 32 % (g * N) == 0 &&
+           live <= (MODE == M_FUSED ? 32 : 48);
 }
 
 template <int MODE, typename T>

@@ -14,7 +14,8 @@ pytestmark = pytest.mark.gpu
 
 def batch_codes(r, dtype):
     """Variant codes the batch kernels run in every role at width r (the
-    rule of fmm_batch.cu: at most 48 floats live per lane)."""
+    rule of fmm_batch.cu: at most 32 floats live per lane in the forward
+    phase, 48 in the backward phase)."""
     es = 4 if dtype == torch.float32 else 2
     vecs = r * es // 16
     base = max(1, vecs // 32)
@@ -27,7 +28,7 @@ def batch_codes(r, dtype):
         E = V * (16 // es)
         if g & (g - 1) or g * N > 32 or 32 % (g * N):
             continue
-        if E * (2 * U + 2) <= 48 and E * (U + 3) <= 48:
+        if E * (U + 2) <= 32 and E * (2 * U + 2) <= 48 and E * (U + 3) <= 48:
             ok.append(code)
     return ok
 
