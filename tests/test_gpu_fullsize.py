@@ -156,3 +156,70 @@ def test_er_4096_r32_f32_every_output_element():
         for t, name in enumerate(("dA", "dB", "ds")):
             assert_close(f"{k}.{name}", got[k][t], ref[k][t], mag[k][t], 2 * r, dm)
     plan.close()
+
+
+def test_batched_512_matrices_sampled():
+    """The batched configuration at its full size, in the launch the bench
+    times: 512 uneven matrices (half ER, half R-MAT, BF16 A and B, r in
+    {32, 64, 128}), forward and backward each one persistent launch.  Sampled
+    rows (FusedMMA, dA, ds) and columns (dB) of sampled matrices, the largest
+    among them, against the oracle on the BF16-rounded inputs."""
+    from paper_2203_07673_gb300 import fmm
+    dev = torch.device("cuda")
+    items = []
+    for t, sp in enumerate(wl.batched_specs(512)):
+        m = wl.batched_matrix_torch(sp, t, dev)
+        r = m["r"]
+        plan = fmm.Plan(m["row_ptr"], m["col_idx"], m["n"], r, torch.bfloat16,
+                        split_nnz=1 << 30)
+        g = torch.Generator(device=dev)
+        g.manual_seed(7919 * t + 1)
+        items.append(dict(plan=plan, vals=m["vals"], A=m["A"].bfloat16().contiguous(),
+                          B=m["B"].bfloat16().contiguous(),
+                          G=torch.randn(m["m"], r, device=dev, generator=g),
+                          out=torch.empty(m["m"], r, device=dev),
+                          dA=torch.empty(m["m"], r, device=dev),
+                          dB=torch.empty(m["n"], r, device=dev),
+                          ds=torch.empty(m["col_idx"].numel(), device=dev),
+                          rp=m["row_ptr"], ci=m["col_idx"]))
+    keys = ("plan", "vals", "A", "B", "out", "G", "dA", "dB", "ds")
+    batch = fmm.Batch([{k: it[k] for k in keys} for it in items])
+    batch.forward()
+    batch.backward()
+    torch.cuda.synchronize()
+
+    rng = np.random.default_rng(4)
+    nnz = [it["ci"].numel() for it in items]
+    picked = sorted(set(rng.choice(len(items), 6, replace=False).tolist()) |
+                    {int(np.argmax(nnz))})
+    host = lambda x: x.detach().double().cpu().numpy()   # noqa: E731
+    for t in picked:
+        it = items[t]
+        p = it["plan"]
+        S = wl.CSR(p.m, p.n, it["rp"].cpu().numpy().astype(np.int32),
+                   it["ci"].cpu().numpy().astype(np.int32))
+        vals = host(it["vals"])
+        A, B, G = host(it["A"]), host(it["B"]), host(it["G"])
+        deg = int(S.degrees().max())
+        cdeg = int(np.bincount(S.col_idx, minlength=S.n).max())
+        rows = np.unique(np.concatenate([rng.choice(S.m, min(128, S.m), replace=False),
+                                         [int(np.argmax(S.degrees()))]]))
+        rp, ci, v, cused, idx = rows_problem(S, rows, vals)
+        ref = oracle.fusedmm(rp, ci, v, A[rows], B[cused], len(cused))
+        mag = oracle.fusedmm(rp, ci, np.abs(v), np.abs(A[rows]), np.abs(B[cused]), len(cused))
+        _cmp(f"batch {t} FusedMMA rows", host(it["out"])[rows], ref, mag, p.r + deg + 4)
+        dA_r, _, ds_r = oracle.fusedmm_grad(rp, ci, v, A[rows], B[cused], G[rows], len(cused))
+        dA_m, _, ds_m = oracle.fusedmm_grad(rp, ci, np.abs(v), np.abs(A[rows]),
+                                            np.abs(B[cused]), np.abs(G[rows]), len(cused))
+        _cmp(f"batch {t} dA rows", host(it["dA"])[rows], dA_r, dA_m, 2 * p.r + deg + 4)
+        _cmp(f"batch {t} ds", host(it["ds"])[idx], ds_r, ds_m, 2 * p.r + 4)
+        cols = np.unique(np.concatenate([rng.choice(S.n, min(128, S.n), replace=False),
+                                         [int(np.argmax(np.bincount(S.col_idx, minlength=S.n)))]]))
+        rp, ci, v, rused, _ = cols_problem(S, cols, vals)
+        _, dB_c, _ = oracle.fusedmm_grad(rp, ci, v, A[rused], B[cols], G[rused], len(cols))
+        _, dB_m, _ = oracle.fusedmm_grad(rp, ci, np.abs(v), np.abs(A[rused]), np.abs(B[cols]),
+                                         np.abs(G[rused]), len(cols))
+        _cmp(f"batch {t} dB cols", host(it["dB"])[cols], dB_c, dB_m, 2 * p.r + cdeg + 4)
+    batch.close()
+    for it in items:
+        it["plan"].close()
