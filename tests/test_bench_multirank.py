@@ -1,7 +1,9 @@
 """The multi-rank parts of bench.py on CPU: two gloo ranks, max-over-ranks
 timing and the whole-job throughput formula (no GPU involved)."""
+import json
 import os
 import socket
+import sys
 
 import pytest
 import torch.multiprocessing as mp
@@ -49,3 +51,36 @@ def test_whole_job_value_formula():
     # 2 ranks x 10 steps x 100 units, slowest rank 4 ms -> 2000 units / 0.004 s
     assert bench.whole_job_value(100.0, 10, 2, 4.0) == pytest.approx(5e5)
     assert bench.reduce_max([1.0, 2.0], "cpu", 1) == [1.0, 2.0]
+
+
+def _bench(env_extra, *args):
+    import subprocess
+    env = dict(os.environ, **env_extra)
+    return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                           "--workload", "1", "--scale", "0.25", "--steps", "1", "--warmup", "3",
+                           *args], capture_output=True, text=True, env=env, timeout=300)
+
+
+def test_reference_arm_prints_on_rank_zero_only():
+    """The reference arm (the FP64 oracle on host cores) runs on rank 0; under
+    torchrun the other ranks exit 0 without work and print nothing."""
+    other = _bench({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
+    assert other.returncode == 0, other.stderr
+    assert other.stdout.strip() == ""
+    first = _bench({"RANK": "0", "WORLD_SIZE": "1", "LOCAL_RANK": "0"})
+    assert first.returncode == 0, first.stderr
+    lines = [line for line in first.stdout.splitlines() if line.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == bench_unit()
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+    for k in ("metric", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config"):
+        assert k in d, k
+
+
+def bench_unit():
+    sys.path.insert(0, ROOT)
+    import bench
+    return bench.UNIT
