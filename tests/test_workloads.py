@@ -83,3 +83,31 @@ def test_small_workloads():
     assert len(specs) == 16 and {s["r"] for s in specs} <= {32, 64, 128}
     m0 = wl.batched_matrix(specs[1], 1)
     _valid(m0["S"])
+
+
+def test_torch_generators_on_cpu():
+    """The device generators of the batched and GAT inputs (run here on the
+    CPU device): valid CSR, distinct sorted columns where the recipe says so,
+    seeded, and the batched matrix of a spec has the spec's shape."""
+    import torch
+    g = wl._torch_gen("cpu", 5)
+    rp, ci = wl.er_exact_degree_torch(300, 257, 32, g, "cpu")
+    S = wl.CSR(300, 257, rp.numpy().astype(np.int32), ci.numpy().astype(np.int32))
+    _valid(S)
+    assert np.all(S.degrees() == 32)
+    _distinct_sorted(S)
+    rp, ci = wl.rmat_torch(10, 16 * 1000, 0.57, 0.19, 0.19, wl._torch_gen("cpu", 6), "cpu", 1000)
+    R = wl.CSR(1000, 1000, rp.numpy().astype(np.int32), ci.numpy().astype(np.int32))
+    _valid(R)
+    _distinct_sorted(R)
+    assert R.degrees().max() > 10 * R.degrees().mean()
+    rp2, ci2 = wl.rmat_torch(10, 16 * 1000, 0.57, 0.19, 0.19, wl._torch_gen("cpu", 6), "cpu", 1000)
+    assert torch.equal(rp, rp2) and torch.equal(ci, ci2)
+    specs = wl.batched_specs(8, scale_rows=0.01)
+    for t in (0, 1):
+        m = wl.batched_matrix_torch(specs[t], t, "cpu")
+        assert m["m"] == m["n"] == specs[t]["rows"] and m["r"] == specs[t]["r"]
+        assert m["A"].shape == (m["m"], m["r"]) and m["vals"].numel() == m["col_idx"].numel()
+        B = wl.CSR(m["m"], m["n"], m["row_ptr"].numpy().astype(np.int32),
+                   m["col_idx"].numpy().astype(np.int32))
+        _valid(B)
