@@ -18,6 +18,8 @@ Functions (all return float64 numpy arrays):
   fusedmm_grad(rowptr, colidx, vals, A, B, G, n)     -> (dA, dB, ds)
   fusedmm_t_grad(rowptr, colidx, vals, A, B, Gn, n)  -> (dA, dB, ds)
   als_cg(rowptr, colidx, c, A, B, lam, iters, side)  -> updated A (side 0) or B (side 1)
+  als_cg_state(rowptr, colidx, c, A, B, lam, iters, side, state=None)
+                                              -> (X, res, p, rs): the same CG with its state
   gat(rowptr, colidx, vals, f, g, H, heads, slope)   -> out[m, heads * rh]  (GAT forward)
 ``vals=None`` means every value of S is 1.
 """
@@ -73,6 +75,9 @@ def _load():
                                       ptr, ptr, ptr, ptr],
             "oracle_als_cg": [i64, i64, i64, ptr, ptr, ptr, ptr, ptr, ctypes.c_double,
                               i64, ctypes.c_int],
+            "oracle_als_cg_state": [i64, i64, i64, ptr, ptr, ptr, ptr, ptr,
+                                    ctypes.c_double, i64, ctypes.c_int, ctypes.c_int,
+                                    ptr, ptr, ptr],
             "oracle_gat": [i64, i64, i64, i64, ptr, ptr, ptr, ptr, ptr, ptr, ctypes.c_double,
                            ptr],
         }
@@ -213,6 +218,34 @@ def als_cg(rowptr, colidx, c, A, B, lam, iters, side):
     _run(_load().oracle_als_cg, m, n, r, _p(rowptr), _p(colidx), _p(c), _p(A), _p(B),
          float(lam), int(iters), int(side))
     return A if side == 0 else B
+
+
+def als_cg_state(rowptr, colidx, c, A, B, lam, iters, side, state=None):
+    """The CG of als_cg with its state exposed (Sec. VI-E).  With state=None
+    it starts from the current rows of the side (r = b - M x, p = r,
+    rs = <r, r>) and runs `iters` iterations; with state=(res, p, rs) it
+    continues from that state (c is then not read).  Returns
+    (X, res, p, rs): the updated side and the state after the last
+    iteration, all float64 copies."""
+    rowptr, colidx, m = _prep(rowptr, colidx, A)
+    A = _dims(A, m).copy()
+    B = _f64(B).copy()
+    n = B.shape[0]
+    r = A.shape[1]
+    rows = m if side == 0 else n
+    if state is None:
+        res, p, rs = np.zeros((rows, r)), np.zeros((rows, r)), np.zeros(rows)
+        init = 1
+        c = _f64(c)
+    else:
+        res = _f64(state[0]).reshape(rows, r).copy()
+        p = _f64(state[1]).reshape(rows, r).copy()
+        rs = _f64(state[2]).reshape(rows).copy()
+        init = 0
+        c = None
+    _run(_load().oracle_als_cg_state, m, n, r, _p(rowptr), _p(colidx), _p(c), _p(A), _p(B),
+         float(lam), int(iters), int(side), init, _p(res), _p(p), _p(rs))
+    return (A if side == 0 else B), res, p, rs
 
 
 def gat(rowptr, colidx, vals, f, g, H, heads, slope):

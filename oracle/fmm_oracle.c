@@ -284,11 +284,20 @@ static void oracle_apply_m(int64_t r, double lambda, int64_t deg, const int64_t 
     }
 }
 
-int oracle_als_cg(int64_t m, int64_t n, int64_t r, const int64_t *rowptr,
-                  const int64_t *colidx, const double *c, double *A, double *B,
-                  double lambda, int64_t iters, int side)
+/* The CG of every row of one side, with its state exposed.  When init is
+ * set the state starts from the current rows:  r = b - M x;  p = r;
+ * rs = <r, r>;  otherwise res, p (rows x r) and rs (rows) hold the state
+ * of an earlier call.  Then `iters` iterations as above.  res, p and rs
+ * may be NULL when init is set (the state is then kept internally and
+ * dropped on return). */
+static int oracle_als_cg_core(int64_t m, int64_t n, int64_t r, const int64_t *rowptr,
+                              const int64_t *colidx, const double *c, double *A, double *B,
+                              double lambda, int64_t iters, int side, int init,
+                              double *res_io, double *p_io, double *rs_io)
 {
     if (oracle_check(m, n, rowptr, colidx))
+        return -1;
+    if (!init && (!res_io || !p_io || !rs_io))
         return -1;
     int64_t nnz = rowptr[m];
     /* neighbour lists of every row of the side being updated */
@@ -306,7 +315,7 @@ int oracle_als_cg(int64_t m, int64_t n, int64_t r, const int64_t *rowptr,
             start[i] = rowptr[i];
         for (int64_t p = 0; p < nnz; ++p) {
             nbr[p] = colidx[p];
-            cv[p] = c[p];
+            cv[p] = c ? c[p] : 0.0;
         }
     } else {
         for (int64_t p = 0; p < nnz; ++p)
@@ -319,28 +328,35 @@ int oracle_als_cg(int64_t m, int64_t n, int64_t r, const int64_t *rowptr,
                 int64_t j = colidx[p];
                 int64_t q = start[j] + fill[j]++;
                 nbr[q] = i;
-                cv[q] = c[p];
+                cv[q] = c ? c[p] : 0.0;
             }
         free(fill);
     }
     double *X = side == 0 ? A : B;
     const double *Y = side == 0 ? B : A;
-    double *res = w, *pp = w + r, *q = w + 2 * r, *bb = w + 3 * r;
+    double *q = w + 2 * r, *bb = w + 3 * r;
     for (int64_t i = 0; i < rows; ++i) {
         int64_t deg = start[i + 1] - start[i];
         const int64_t *nb = nbr + start[i];
         double *x = X + i * r;
-        for (int64_t k = 0; k < r; ++k)
-            bb[k] = 0.0;
-        for (int64_t t = 0; t < deg; ++t)
+        double *res = res_io ? res_io + i * r : w;
+        double *pp = p_io ? p_io + i * r : w + r;
+        double rs;
+        if (init) {
             for (int64_t k = 0; k < r; ++k)
-                bb[k] += cv[start[i] + t] * Y[nb[t] * r + k];
-        oracle_apply_m(r, lambda, deg, nb, Y, x, q);
-        for (int64_t k = 0; k < r; ++k) {
-            res[k] = bb[k] - q[k];
-            pp[k] = res[k];
+                bb[k] = 0.0;
+            for (int64_t t = 0; t < deg; ++t)
+                for (int64_t k = 0; k < r; ++k)
+                    bb[k] += cv[start[i] + t] * Y[nb[t] * r + k];
+            oracle_apply_m(r, lambda, deg, nb, Y, x, q);
+            for (int64_t k = 0; k < r; ++k) {
+                res[k] = bb[k] - q[k];
+                pp[k] = res[k];
+            }
+            rs = oracle_dot(res, res, r);
+        } else {
+            rs = rs_io[i];
         }
-        double rs = oracle_dot(res, res, r);
         for (int64_t it = 0; it < iters; ++it) {
             oracle_apply_m(r, lambda, deg, nb, Y, pp, q);
             double pq = oracle_dot(pp, q, r);
@@ -355,9 +371,34 @@ int oracle_als_cg(int64_t m, int64_t n, int64_t r, const int64_t *rowptr,
                 pp[k] = res[k] + beta * pp[k];
             rs = rs2;
         }
+        if (rs_io)
+            rs_io[i] = rs;
     }
     free(start); free(nbr); free(cv); free(w);
     return 0;
+}
+
+int oracle_als_cg(int64_t m, int64_t n, int64_t r, const int64_t *rowptr,
+                  const int64_t *colidx, const double *c, double *A, double *B,
+                  double lambda, int64_t iters, int side)
+{
+    return oracle_als_cg_core(m, n, r, rowptr, colidx, c, A, B, lambda, iters, side, 1,
+                              NULL, NULL, NULL);
+}
+
+/* The same CG with its state in the caller's arrays: init = 1 starts from
+ * the current rows (c is read) and writes the state after `iters`
+ * iterations into res, p (rows x r) and rs (rows); init = 0 continues from
+ * the state given there (c is not read and may be NULL). */
+int oracle_als_cg_state(int64_t m, int64_t n, int64_t r, const int64_t *rowptr,
+                        const int64_t *colidx, const double *c, double *A, double *B,
+                        double lambda, int64_t iters, int side, int init, double *res,
+                        double *p, double *rs)
+{
+    if (!res || !p || !rs)
+        return -1;
+    return oracle_als_cg_core(m, n, r, rowptr, colidx, c, A, B, lambda, iters, side, init,
+                              res, p, rs);
 }
 
 /* ---------------------------------------------------------------------------

@@ -90,3 +90,75 @@ def test_als_loss_decreases():
         cur = loss(A, B)
         assert cur <= prev + 1e-9
         prev = cur
+
+
+def _rows_of_side(S, c, A, B, side):
+    """Per row of the side: (neighbour rows of the fixed factor, observations)."""
+    M = sp.csr_matrix((c, S.col_idx, S.row_ptr), shape=(S.m, S.n))
+    if side == 1:
+        M, A, B = M.T.tocsr(), B, A
+    P = sp.csr_matrix((np.ones(M.nnz), M.indices, M.indptr), shape=M.shape)
+    out = []
+    for i in range(M.shape[0]):
+        nb = P.indices[P.indptr[i]:P.indptr[i + 1]]
+        out.append((nb, M.data[M.indptr[i]:M.indptr[i + 1]]))
+    return out, A, B
+
+
+@pytest.mark.parametrize("side", [0, 1])
+def test_cg_state_after_init_is_the_residual(side):
+    """init: res = b - (Y^T Y + lam I) x with b = Y^T c, p = res, rs = |res|^2,
+    built per row from dense products."""
+    S, c, A, B = _problem(6 + side)
+    lam = 0.4
+    X, res, p, rs = oracle.als_cg_state(S.row_ptr, S.col_idx, c, A, B, lam, 0, side)
+    rows, Xin, Y = _rows_of_side(S, c, A, B, side)
+    np.testing.assert_array_equal(X, Xin)
+    for i, (nb, cv) in enumerate(rows):
+        Mi = Y[nb].T @ Y[nb] + lam * np.eye(Y.shape[1])
+        exp = Y[nb].T @ cv - Mi @ Xin[i]
+        np.testing.assert_allclose(res[i], exp, rtol=1e-12, atol=1e-12)
+        np.testing.assert_array_equal(p[i], res[i])
+        np.testing.assert_allclose(rs[i], exp @ exp, rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("side", [0, 1])
+def test_cg_steps_from_passed_state_reach_the_dense_solution(side):
+    """r single iterations, each continuing from the state the previous call
+    returned, solve every row's r x r system exactly (exact arithmetic): the
+    state (res, p, rs) is carried between calls correctly."""
+    S, c, A, B = _problem(8 + side)
+    lam = 0.5
+    exact = _dense_solution(S, c, A, B, lam, side)
+    X, res, p, rs = oracle.als_cg_state(S.row_ptr, S.col_idx, c, A, B, lam, 0, side)
+    for _ in range(A.shape[1]):
+        Ain, Bin = (X, B) if side == 0 else (A, X)
+        X, res, p, rs = oracle.als_cg_state(S.row_ptr, S.col_idx, None, Ain, Bin, lam, 1, side,
+                                            state=(res, p, rs))
+    np.testing.assert_allclose(X, exact, rtol=1e-7, atol=1e-9)
+
+
+def test_one_step_from_state_closed_form():
+    """From x = 0 (res = p = b, rs = |b|^2) one iteration gives
+    alpha = |b|^2 / b^T M b, x = alpha b, res = b - alpha M b,
+    p = res + (|res|^2 / |b|^2) b."""
+    S, c, A, B = _problem(10)
+    lam = 0.3
+    rows, _, Y = _rows_of_side(S, c, A, B, 0)
+    b = np.zeros_like(A)
+    for i, (nb, cv) in enumerate(rows):
+        b[i] = Y[nb].T @ cv
+    rs0 = np.einsum("ij,ij->i", b, b)
+    X, res, p, rs = oracle.als_cg_state(S.row_ptr, S.col_idx, None, np.zeros_like(A), B, lam,
+                                        1, 0, state=(b, b, rs0))
+    for i, (nb, _) in enumerate(rows):
+        Mb = Y[nb].T @ (Y[nb] @ b[i]) + lam * b[i]
+        den = b[i] @ Mb
+        alpha = rs0[i] / den if den > 0 else 0.0
+        res_e = b[i] - alpha * Mb
+        rs_e = res_e @ res_e
+        p_e = res_e + (rs_e / rs0[i] if rs0[i] > 0 else 0.0) * b[i]
+        np.testing.assert_allclose(X[i], alpha * b[i], rtol=1e-12, atol=1e-14)
+        np.testing.assert_allclose(res[i], res_e, rtol=1e-11, atol=1e-12)
+        np.testing.assert_allclose(p[i], p_e, rtol=1e-11, atol=1e-12)
+        np.testing.assert_allclose(rs[i], rs_e, rtol=1e-10, atol=1e-14)
