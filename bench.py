@@ -674,6 +674,8 @@ def run_fmm(args, rank, world, local_rank):
                                     "unfused": "fmm_sddmm + fmm_spmm"}
     if w["dtype"] == "bf16":
         line["dtype"] = "f32 (bf16 inputs)"
+    if k == 2 and not args.no_zipf:
+        line["c4"] = zipf_section(args, dev, stream)
     if rank == 0 and not args.no_cpu_baseline:
         cv, desc, threads, _ = oracle_sample(w, args.cpu_seconds)
         line["cpu_baseline"] = {"value": cv, "unit": UNIT, "cores": threads, "kind": "oracle",
@@ -683,6 +685,85 @@ def run_fmm(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
     plan.close()
     return 0
+
+
+def zipf_section(args, dev, stream):
+    """The Zipf-row workload (2^21 x 2^19, 80M nonzeros, r = 64), drawn on
+    the device, in float32 and with bfloat16 A and B: FusedMMA and FusedMMB
+    (with the per-call value permutation, and with registered values, i.e.
+    the pass alone) timed with CUDA events, each pass beside the gather probe
+    on its own index stream (the rows it fetches, in its order, from the same
+    table: B for FusedMMA, A in S^T order for FusedMMB)."""
+    import torch
+
+    from paper_2203_07673_gb300 import fmm
+    from paper_2203_07673_gb300 import workloads as wl
+
+    w = wl.zipf_workload_torch(dev, scale_rows=args.scale)
+    rp, ci, vals = w["row_ptr"], w["col_idx"], w["vals"]
+    m, n, r, nnz = w["m"], w["n"], w["r"], ci.numel()
+    deg = (rp[1:] - rp[:-1]).long()
+    rows_t = torch.repeat_interleave(torch.arange(m, device=dev, dtype=torch.int32), deg)
+    rows_t = rows_t[torch.argsort(ci, stable=True)].contiguous()
+    peak, _ = load_peaks()
+    reps = max(5, min(args.steps, 20))
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(reps):
+            fn()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        return a0.elapsed_time(a1) / reps
+
+    res = {"workload": w["name"], "m": m, "n": n, "nnz": nnz, "r": r,
+           "max_row_nnz": int(deg.max()), "reps": reps,
+           "note": "l2_gather_frac = probe time / pass time: the pass's gather rate as a "
+                   "fraction of the rate the same index stream reaches with no arithmetic "
+                   "(B, 128 / 64 MiB, mostly L2-resident); gather_ceiling_frac_t the same for "
+                   "the FusedMMB pass (A in S^T order, 512 / 256 MiB)"}
+    for key, tdt, e in (("fp32", torch.float32, 4), ("bf16", torch.bfloat16, 2)):
+        A = w["A"].to(tdt).contiguous()
+        B = w["B"].to(tdt).contiguous()
+        plan = fmm.Plan(rp, ci, n, r, tdt)
+        o = torch.empty(m, r, device=dev)
+        ot = torch.empty(n, r, device=dev)
+        t_f = timed(lambda: fmm.fusedmm(plan, vals, A, B, out=o))
+        t_t = timed(lambda: fmm.fusedmm_t(plan, vals, A, B, out=ot))
+        plan.set_values(vals)
+        t_tr = timed(lambda: fmm.fusedmm_t(plan, vals, A, B, out=ot))
+        plan.set_values(None)
+        p_f = timed(lambda: fmm.probe_gather(B, ci))
+        p_t = timed(lambda: fmm.probe_gather(A, rows_t))
+        model_f = gather_model_bytes(m, nnz, r, e, True)
+        model_t = gather_model_bytes(n, nnz, r, e, True)
+        name = w["name"] + (" [BF16 A,B]" if key == "bf16" else "")
+        tr_f, _ = read_traffic(name, "fmm_fusedmm", key.replace("fp", "f"))
+        tr_t, _ = read_traffic(name, "fmm_fusedmm_t", key.replace("fp", "f"))
+        info = plan.info()
+        res[key] = {
+            "fused_ms": t_f, "fused_t_ms": t_t, "fused_t_registered_values_ms": t_tr,
+            "permute_ms": t_t - t_tr,
+            "gathered_GBs": nnz * r * e / (t_f / 1e3) / 1e9,
+            "gathered_GBs_t": nnz * r * e / (t_tr / 1e3) / 1e9,
+            "model_frac": model_f / (t_f / 1e3) / 1e9 / peak,
+            "model_frac_t": model_t / (t_tr / 1e3) / 1e9 / peak,
+            "probe_ms": p_f, "probe_GBs": nnz * r * e / (p_f / 1e3) / 1e9,
+            "probe_t_ms": p_t, "probe_t_GBs": nnz * r * e / (p_t / 1e3) / 1e9,
+            "l2_gather_frac": p_f / t_f, "gather_ceiling_frac_t": p_t / t_tr,
+            "dram_frac": None if tr_f is None else tr_f / (t_f / 1e3) / 1e9 / peak,
+            "dram_frac_t": None if tr_t is None else tr_t / (t_t / 1e3) / 1e9 / peak,
+            "variant": info["variant"], "variant_t": info["variant_t"],
+            "split_nnz": info["split_nnz"],
+        }
+        plan.close()
+        del A, B, o, ot
+    return res
 
 
 def run_batched(args, rank, world, local_rank):
@@ -1188,6 +1269,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--clock-log", default=None,
                     help="keep nvidia-smi's raw clock samples under this path prefix")
+    ap.add_argument("--no-zipf", action="store_true",
+                    help="default workload without the Zipf-row (c4) section")
     ap.add_argument("--no-library", action="store_true",
                     help="skip the cuSPARSE (torch.sparse) comparison")
     args = ap.parse_args()

@@ -347,13 +347,28 @@ int fmm_gat_project(int32_t rows, int32_t heads, int32_t rh, const float *X, con
  * ch = max(512, ceil(2 nnz / min(65536, 8388608 / r))) nonzeros are split
  * into chunks whose partial rows live there.  r > 65536 returns
  * FMM_EOVERFLOW.  The array is shared by all calls: calls that overlap on the
- * GPU race and give wrong results, so order them on one stream.  The first
- * call on each device looks the array's address up (cudaGetSymbolAddress)
- * with that device current; make it before any stream capture.
+ * GPU race and give wrong results, so order them on one stream.  Every
+ * call looks the array's address up (cudaGetSymbolAddress, which allocates
+ * nothing) on the current device, so the call still finds it after
+ * cudaDeviceReset; the first call on a device may load the library's module
+ * there, so make that first call before any stream capture.
  * Asynchronous on the stream; deterministic.
  */
 int fmm_fusedmm_noalloc(const fmm_csr *S, int32_t r, int32_t dtype, const float *vals,
                         const void *A, const void *B, float *out_m, fmm_stream stream);
+
+/*
+ * Gather-rate probe (a measurement aid; the paper has no counterpart): for
+ * k < count, fetches row idx[k] (row_bytes bytes, 16-byte vectors, the
+ * read-only path the row passes use) of `table` (rows x row_bytes, 16-byte
+ * aligned, device) and does nothing else with it, so its time is the
+ * ceiling for the gather part of a row pass walking the same index list.
+ * row_bytes is 64, 128, 256 or 512; idx (count int32, device) is clamped
+ * into [0, rows).  sink (one uint32, device) may be written.  Asynchronous
+ * on the stream.
+ */
+int fmm_probe_gather(const void *table, int64_t rows, int32_t row_bytes, const int32_t *idx,
+                     int64_t count, uint32_t *sink, fmm_stream stream);
 
 /* Static description of a status code (never NULL). */
 const char *fmm_status_string(int status);

@@ -32,25 +32,46 @@ class ALS:
         self._work = [torch.empty(rows, r, device=dev) for _ in range(4)]
         self._rs = torch.empty(rows, device=dev)
 
-    def _side(self, side: int, iters: int):
-        p_, m, n = self.plan, self.plan.m, self.plan.n
-        rows = m if side == 0 else n
+    def start(self, side: int):
+        """CG set-up of one side (0: rows of A, 1: rows of B): b = SpMM of the
+        observations, q = the FusedMM of the current rows, then
+        res = b - q - lam x, p = res, rs = <res, res> (fmm_cg_init)."""
+        p_, rows = self.plan, self._rows(side)
         X = self.A if side == 0 else self.B
         b, res, p, q = (w[:rows] for w in self._work)
-        rs = self._rs[:rows]
         if side == 0:
             fmm.spmm(p_, self.c, self.B, out=b)
             fmm.fusedmm(p_, None, self.A, self.B, out=q)
         else:
             fmm.spmm_t(p_, self.c, self.A, out=b)
             fmm.fusedmm_t(p_, None, self.A, self.B, out=q)
-        fmm.cg_init(self.lam, b, q, X, res, p, rs)
+        fmm.cg_init(self.lam, b, q, X, res, p, self._rs[:rows])
+
+    def iterate(self, side: int, iters: int):
+        """`iters` CG iterations of one side from the state left by start()
+        or an earlier iterate(): q = the FusedMM of p, then fmm_cg_update."""
+        p_, rows = self.plan, self._rows(side)
+        X = self.A if side == 0 else self.B
+        _, res, p, q = (w[:rows] for w in self._work)
+        rs = self._rs[:rows]
         for _ in range(iters):
             if side == 0:
                 fmm.fusedmm(p_, None, p, self.B, out=q)
             else:
                 fmm.fusedmm_t(p_, None, self.A, p, out=q)
             fmm.cg_update(self.lam, X, res, p, q, rs)
+
+    def state(self, side: int):
+        """Views of the CG state of a side: (res, p, rs)."""
+        rows = self._rows(side)
+        return self._work[1][:rows], self._work[2][:rows], self._rs[:rows]
+
+    def _rows(self, side: int) -> int:
+        return self.plan.m if side == 0 else self.plan.n
+
+    def _side(self, side: int, iters: int):
+        self.start(side)
+        self.iterate(side, iters)
 
     def update_a(self, iters: int = 10):
         self._side(0, iters)

@@ -1,4 +1,5 @@
 // C-ABI entry points of libfmm (declared in include/fmm.h).
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 
@@ -8,16 +9,39 @@ namespace fmm {
 
 bool fast_r(int32_t r) { return r == 32 || r == 64 || r == 128 || r == 256; }
 
+int sm_count()
+{
+    static std::atomic<int> cached[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return 1;
+    if (dev >= 0 && dev < 64) {
+        const int c = cached[dev].load(std::memory_order_relaxed);
+        if (c > 0)
+            return c;
+    }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms <= 0)
+        return 1;
+    if (dev >= 0 && dev < 64)
+        cached[dev].store(sms, std::memory_order_relaxed);
+    return sms;
+}
+
 static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 // Variant codes: vectors-per-lane multiple * 100 + groups per team * 10 +
 // nonzeros per group per batch (the combinations instantiated in
 // fmm_rows.cuh; a combination that does not fit a row shape falls back to
 // the shape's default); 1000 + ring depth * 10 + vectors-per-lane multiple
-// for the staged pass (fmm_staged.cuh), whose backward roles run the team
-// kernel with 2 nonzeros per batch.
+// for the staged pass (fmm_staged.cuh); 2000 + register-ring batches * 100 +
+// nonzeros per batch * 10 + vectors-per-lane multiple for the pipelined pass
+// (fmm_pipe.cuh).  The backward roles of staged and pipelined codes run the
+// team kernel with one group per row and 2 nonzeros per batch.
 static const int kVariantCodes[] = {114, 118, 222, 224, 441, 442, 214, 124, 112, 122, 212, 221,
-                                    1041, 1042, 1081, 1082};
+                                    1041, 1042, 1081, 1082,
+                                    2221, 2421, 2211, 2411, 2222, 2212};
 
 bool variant_known(int code)
 {
@@ -29,6 +53,13 @@ bool variant_known(int code)
 KernelVariant decode_variant(int code)
 {
     KernelVariant v;
+    if (code >= 2000) {
+        v.ring = (code / 100) % 10;
+        v.u = (code / 10) % 10;
+        v.vpl_mult = code % 10;
+        v.ng = 1;
+        return v;
+    }
     if (code >= 1000) {
         v.stages = (code / 10) % 100;
         v.vpl_mult = code % 10;
@@ -44,6 +75,8 @@ KernelVariant decode_variant(int code)
 
 int encode_variant(const KernelVariant &v)
 {
+    if (v.ring > 0)
+        return 2000 + v.ring * 100 + v.u * 10 + v.vpl_mult;
     if (v.stages > 0)
         return 1000 + v.stages * 10 + v.vpl_mult;
     return v.vpl_mult * 100 + v.ng * 10 + v.u;
@@ -54,13 +87,24 @@ cudaError_t launch_pass(int mode, int dtype, const KernelVariant &v, const PassA
 {
     const bool vec = fast_r(a.r) && aligned16(a.L) && aligned16(a.Y) && aligned16(a.H) &&
                      aligned16(a.out) && aligned16(a.partials);
-    if (v.stages > 0 && vec && (mode == M_FUSED || mode == M_SDDMM || mode == M_SPMM)) {
+    const bool fwd = mode == M_FUSED || mode == M_SDDMM || mode == M_SPMM;
+    if (v.stages > 0 && vec && fwd) {
         return dtype == FMM_BF16 ? launch_staged_bf16(mode, v.vpl_mult, v.stages, a, st)
                                  : launch_staged_f32(mode, v.vpl_mult, v.stages, a, st);
     }
+    if (v.ring > 0 && vec && fwd) {
+        const cudaError_t e = dtype == FMM_BF16
+                                  ? launch_pipe_bf16(mode, v.vpl_mult, v.u, v.ring, a, st)
+                                  : launch_pipe_f32(mode, v.vpl_mult, v.u, v.ring, a, st);
+        if (e != cudaErrorNotSupported)
+            return e;
+        // a ring layout this width does not have: the team kernel below
+    }
+    // backward roles of a staged or pipelined plan: one group, 2 per batch
+    const int u = (v.stages > 0 || v.ring > 0) ? 2 : v.u;
     if (dtype == FMM_BF16)
-        return launch_pass_bf16(mode, v.vpl_mult, v.ng, v.u, vec, a, st);
-    return launch_pass_f32(mode, v.vpl_mult, v.ng, v.u, vec, a, st);
+        return launch_pass_bf16(mode, v.vpl_mult, v.ng, u, vec, a, st);
+    return launch_pass_f32(mode, v.vpl_mult, v.ng, u, vec, a, st);
 }
 
 }  // namespace fmm

@@ -161,6 +161,7 @@ int batch_code(int dtype, int mode, int r, const KernelVariant &v)
     // pass only), with fewer nonzeros per batch if needed
     KernelVariant d = default_variant(r, dtype, 0.0);
     d.stages = 0;
+    d.ring = 0;
     for (int u : {d.u, 2, 1}) {
         d.u = u;
         const int c = encode_variant(d);

@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(256) cg_update_vec(int32_t rows, int32_t r, fl
 static unsigned cg_blocks(int32_t rows)
 {
     const int64_t b = ((int64_t)rows + 7) / 8;
-    return (unsigned)std::min<int64_t>(std::max<int64_t>(b, 1), 152 * 64);
+    return (unsigned)std::min<int64_t>(std::max<int64_t>(b, 1), (int64_t)sm_count() * 64);
 }
 
 }  // namespace fmm

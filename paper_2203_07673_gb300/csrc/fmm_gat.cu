@@ -331,7 +331,7 @@ int fmm_gat_project(int32_t rows, int32_t heads, int32_t rh, const float *X, con
     }
     if (rows == 0)
         return FMM_OK;
-    const int64_t blocks = std::min<int64_t>(((int64_t)rows + 7) / 8, 152 * 64);
+    const int64_t blocks = std::min<int64_t>(((int64_t)rows + 7) / 8, (int64_t)sm_count() * 64);
     gat_project_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(rows, heads, rh, X, w,
                                                                           out);
     cudaError_t e = cudaGetLastError();

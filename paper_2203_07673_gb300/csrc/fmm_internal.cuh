@@ -16,6 +16,8 @@ namespace fmm {
 struct KernelVariant {
     int vpl_mult = 1, ng = 1, u = 8;
     int stages = 0;   // > 0: the staged pass (fmm_staged.cuh) with this ring depth
+    int ring = 0;     // > 0: the pipelined pass (fmm_pipe.cuh), this many batches in
+                      // the register ring (forward roles; u nonzeros per batch)
 };
 
 // One side of a plan: the CSR that a row pass walks (S itself, or S^T with a
@@ -114,6 +116,12 @@ cudaError_t launch_staged_f32(int mode, int vpl_mult, int stages, const PassArgs
                               cudaStream_t st);
 cudaError_t launch_staged_bf16(int mode, int vpl_mult, int stages, const PassArgs &a,
                                cudaStream_t st);
+// Pipelined forward-role passes (fmm_pipe.cuh): FusedMM, SDDMM and SpMM with
+// a register ring of `ring` batches of u gathered rows per team; vector path.
+cudaError_t launch_pipe_f32(int mode, int vpl_mult, int u, int ring, const PassArgs &a,
+                            cudaStream_t st);
+cudaError_t launch_pipe_bf16(int mode, int vpl_mult, int u, int ring, const PassArgs &a,
+                             cudaStream_t st);
 // dst[q] = src[perm[q]] for q < nnz (values of S into the order of S^T).
 cudaError_t launch_permute(const float *src, const int32_t *perm, float *dst, int64_t nnz,
                            cudaStream_t st);
@@ -122,6 +130,9 @@ cudaError_t launch_combine(const Side &side, float *out, int32_t r,
                            cudaStream_t st);
 
 bool fast_r(int32_t r);
+// Streaming multiprocessors of the current device (queried once per device;
+// 1 if the query fails, which keeps grid-stride launches correct).
+int sm_count();
 bool variant_known(int code);
 KernelVariant decode_variant(int code);
 int encode_variant(const KernelVariant &v);

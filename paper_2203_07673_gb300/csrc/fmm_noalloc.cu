@@ -25,11 +25,11 @@
 //
 // Every call uses the same array: calls that overlap on the GPU (two streams,
 // or two host threads without ordering) race on it and give wrong results.
-// Order them on one stream.  The first call on each device looks up the
-// array's device address with cudaGetSymbolAddress, with that device
-// current; make that first call before any stream capture.
+// Order them on one stream.  Every call looks up the array's device address
+// with cudaGetSymbolAddress on the current device (no allocation); the first
+// call on a device may load the library's module there, so make that first
+// call before any stream capture.
 #include <cstdio>
-#include <mutex>
 
 #include "fmm_rows.cuh"
 
@@ -46,7 +46,6 @@ constexpr size_t CHUNKS_OFF = HEADER_BYTES;
 constexpr size_t SPLIT_OFF = CHUNKS_OFF + sizeof(int4) * MAX_CHUNKS;
 constexpr size_t PARTIALS_OFF = SPLIT_OFF + sizeof(int4) * MAX_SPLIT;
 constexpr size_t SCRATCH_BYTES = PARTIALS_OFF + sizeof(float) * PARTIAL_FLOATS;
-constexpr int MAX_DEVICES = 64;
 
 struct Header {
     int32_t n_chunks;
@@ -306,7 +305,7 @@ void launch_vec(const Args &a, cudaStream_t st)
     const long long blocks = ((long long)a.m * G + 255) / 256;
     if (blocks > 0)
         rows_kernel<T, R, U><<<(unsigned)blocks, 256, 0, st>>>(a);
-    chunks_kernel<T, R, U><<<152 * 8, 256, 0, st>>>(a);
+    chunks_kernel<T, R, U><<<sm_count() * 8, 256, 0, st>>>(a);
 }
 
 template <typename T>
@@ -324,35 +323,21 @@ void launch_typed(const Args &a, bool vec, cudaStream_t st)
     const long long blocks = ((long long)a.m + 7) / 8;
     if (blocks > 0)
         rows_generic<T><<<(unsigned)blocks, 256, 0, st>>>(a);
-    chunks_generic<T><<<152 * 8, 256, 0, st>>>(a);
+    chunks_generic<T><<<sm_count() * 8, 256, 0, st>>>(a);
 }
 
-std::mutex g_mu;
-void *g_base[MAX_DEVICES] = {};
-
+// The array's device address, looked up on every call with the current
+// device (cudaGetSymbolAddress allocates nothing).  Nothing is cached, so a
+// module reloaded at another address (after cudaDeviceReset) is followed.
 int scratch_base(unsigned char **base)
 {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) {
-        set_error("cudaGetDevice", e);
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        set_error("cudaGetSymbolAddress(no-alloc scratch)", e);
         return FMM_ECUDA;
     }
-    if (dev < 0 || dev >= MAX_DEVICES) {
-        set_error_msg("device ordinal beyond the no-alloc table");
-        return FMM_EUNSUPPORTED;
-    }
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_base[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            set_error("cudaGetSymbolAddress(no-alloc scratch)", e);
-            return FMM_ECUDA;
-        }
-        g_base[dev] = p;
-    }
-    *base = static_cast<unsigned char *>(g_base[dev]);
+    *base = static_cast<unsigned char *>(p);
     return FMM_OK;
 }
 
@@ -409,14 +394,14 @@ extern "C" int fmm_fusedmm_noalloc(const fmm_csr *S, int32_t r, int32_t dtype, c
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(base, 0, HEADER_BYTES, st);
     if (e == cudaSuccess) {
-        const long long blocks = std::min<long long>(((long long)S->m + 255) / 256, 152 * 16);
+        const long long blocks = std::min<long long>(((long long)S->m + 255) / 256, (long long)sm_count() * 16);
         setup_kernel<<<(unsigned)blocks, 256, 0, st>>>(a);
         const bool vec = fast_r(r) && aligned16(A) && aligned16(B) && aligned16(out_m);
         if (dtype == FMM_BF16)
             launch_typed<bf16_t>(a, vec, st);
         else
             launch_typed<float>(a, vec, st);
-        combine_kernel<<<152 * 4, 256, 0, st>>>(a);
+        combine_kernel<<<sm_count() * 4, 256, 0, st>>>(a);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) {

@@ -1,0 +1,323 @@
+// Pipelined row pass: the gathered rows of the next batches are already in
+// flight while the current batch is used.
+//
+// The team kernel (fmm_rows.cuh) issues the gathers of a batch and then
+// waits for them, so a team has at most one batch of rows in flight and its
+// warp idles for the whole load latency once per batch.  On patterns whose
+// gathers mostly hit L2 with short dense rows (bfloat16 rows of r = 64,
+// 128 bytes) that wait, not bandwidth, sets the pass time.  Here a team keeps
+// a ring of RING batches of gathered rows in registers, as the raw 16-byte
+// words (bfloat16 rows stay packed until used): while batch b is used, the
+// loads of batches b + 1 .. b + RING - 1 are in flight.  The ring is indexed
+// with compile-time slots only (the loop over one index block is fully
+// unrolled), so it stays in registers.
+//
+// Arithmetic uses the paired float32 instructions (__ffma2_rn, __fadd2_rn:
+// two round-to-nearest operations in one instruction): the partial dot
+// product of a lane runs as two interleaved chains (even and odd elements)
+// summed at the end, the accumulation updates two elements per instruction,
+// and the U dot products of a batch are reduced across the lane group in
+// pairs.
+//
+// Column indices and values come in index blocks of IB nonzeros (K per
+// lane, coalesced) handed out by shuffles; the current and the next block
+// are held, which covers a prefetch distance of up to one block.  Nonzeros
+// past the end of a row get value 0 and a zero row, so every batch runs the
+// same instructions and contributes exactly nothing.
+//
+// Roles: FusedMM, SDDMM, SpMM (the forward roles), one team of G lanes per
+// row or chunk of a split row.
+#pragma once
+
+#include "fmm_rows.cuh"
+
+namespace fmm {
+
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
+// The 16-byte word q of a row of T as float pairs (element 2i, 2i + 1).
+template <typename T>
+__device__ __forceinline__ void unpack2(const uint4 q, float2 *f)
+{
+    if constexpr (sizeof(T) == 2) {
+        f[0] = make_float2(__uint_as_float(q.x << 16), __uint_as_float(q.x & 0xffff0000u));
+        f[1] = make_float2(__uint_as_float(q.y << 16), __uint_as_float(q.y & 0xffff0000u));
+        f[2] = make_float2(__uint_as_float(q.z << 16), __uint_as_float(q.z & 0xffff0000u));
+        f[3] = make_float2(__uint_as_float(q.w << 16), __uint_as_float(q.w & 0xffff0000u));
+    } else {
+        f[0] = make_float2(__uint_as_float(q.x), __uint_as_float(q.y));
+        f[1] = make_float2(__uint_as_float(q.z), __uint_as_float(q.w));
+    }
+}
+
+// Registers a variant keeps per lane, in floats: the ring (raw words), the
+// local row, the accumulator and one unpacked batch.
+template <typename T, int VPL, int U, int RING>
+constexpr int pipe_live_floats()
+{
+    return RING * U * VPL * 4 + 2 * VPL * Elem<T>::PER16 + U * VPL * Elem<T>::PER16;
+}
+
+// Blocks of 256 threads asked to stay resident per SM: as many as the
+// register estimate allows, at most 5 (48 registers a thread).
+template <typename T, int VPL, int U, int RING>
+constexpr int pipe_min_blocks()
+{
+    constexpr int regs = pipe_live_floats<T, VPL, U, RING>() + 24;
+    return regs <= 48 ? 5 : regs <= 64 ? 4 : regs <= 80 ? 3 : regs <= 128 ? 2 : 1;
+}
+
+template <int MODE, typename T, int R, int VPL, int U, int RING>
+__global__ void __launch_bounds__(256, (pipe_min_blocks<T, VPL, U, RING>()))
+    pipe_pass_kernel(const PassArgs a)
+{
+    static_assert(MODE == M_FUSED || MODE == M_SDDMM || MODE == M_SPMM, "forward roles");
+    using TS = TeamShape<T, R, VPL, 1>;
+    constexpr int G = TS::G, E = TS::E, EPV = TS::EPV;
+    constexpr int E2 = E / 2, W2 = EPV / 2;   // float pairs per lane; per 16-byte word
+    constexpr int K = G >= 8 ? 1 : 8 / G;     // index entries per lane per block
+    constexpr int IB = K * G;                 // nonzeros per index block
+    constexpr int BPB = IB / U;               // batches per index block
+    static_assert(IB % U == 0 && BPB % RING == 0 && RING >= 2, "ring layout");
+    constexpr bool HAS_L = MODE != M_SPMM;
+    constexpr bool ACC = MODE != M_SDDMM;
+    constexpr bool NZ = MODE == M_SDDMM;
+
+    const int lane = threadIdx.x & 31;
+    const int lig = lane & (G - 1);
+    const int tbase = lane & ~(G - 1);
+    const long long gid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const long long total = (long long)a.n_chunks + a.n_light;
+    const bool active = gid < total;
+    const Loader ld;
+
+    int row = 0, beg = 0, end = 0, slot = -1;
+    if (active)
+        pass_item(a, gid, row, beg, end, slot);
+    const T *L = static_cast<const T *>(a.L);
+    const T *Y = static_cast<const T *>(a.Y);
+
+    float2 l2[E2], acc2[E2];
+#pragma unroll
+    for (int e = 0; e < E2; ++e) {
+        l2[e] = make_float2(0.f, 0.f);
+        acc2[e] = make_float2(0.f, 0.f);
+    }
+    if (HAS_L && active && end > beg) {
+#pragma unroll
+        for (int v = 0; v < VPL; ++v) {
+            const uint4 q = ld.u4(reinterpret_cast<const uint4 *>(L + (size_t)row * R) + v * G + lig,
+                                  false);
+            unpack2<T>(q, &l2[v * W2]);
+        }
+    }
+
+    const int n = end - beg;
+    const int wblocks = (int)__reduce_max_sync(0xffffffffu, (unsigned)((n + IB - 1) / IB));
+
+    // index block b: entry e of lane l is nonzero b * IB + e * G + l; past
+    // the end of the row j = -1 and s = 0
+    int jc[K], jn[K], ic[K], in_[K];
+    float sc[K], sn[K];
+    auto load_block = [&](int b, int (&j)[K], float (&s)[K], int (&si)[K]) {
+#pragma unroll
+        for (int e = 0; e < K; ++e) {
+            const int q = b * IB + e * G + lig;
+            j[e] = -1; s[e] = 0.f; si[e] = -1;
+            if (q < n) {
+                const int p = beg + q;
+                j[e] = ld.idx(a.col_idx + p);
+                const int sp = (a.perm && (NZ || !a.s_direct)) ? ld.idx(a.perm + p) : p;
+                si[e] = sp;
+                s[e] = a.s ? ld.val(a.s + (a.s_direct ? p : sp)) : 1.f;
+            }
+        }
+    };
+
+    uint4 ring[RING][U][VPL];
+
+    // gathers of batch bb (block-local) of the block whose indices are j
+    auto issue = [&](uint4 (&dst)[U][VPL], const int (&j)[K], int bb) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int t = bb * U + u;
+            const int jj = __shfl_sync(0xffffffffu, j[t / G], tbase + (t % G));
+#pragma unroll
+            for (int v = 0; v < VPL; ++v) {
+                dst[u][v] = make_uint4(0u, 0u, 0u, 0u);
+                if (jj >= 0)
+                    dst[u][v] = ld.u4(reinterpret_cast<const uint4 *>(Y + (size_t)jj * R) + v * G + lig,
+                                      true);
+            }
+        }
+    };
+
+    load_block(0, jc, sc, ic);
+    load_block(1, jn, sn, in_);
+#pragma unroll
+    for (int b = 0; b < RING - 1; ++b)
+        issue(ring[b], jc, b);
+
+    for (int bk = 0; bk < wblocks; ++bk) {
+#pragma unroll
+        for (int bb = 0; bb < BPB; ++bb) {
+            // prefetch RING - 1 batches ahead, into the slot freed last
+            {
+                const int pf = bb + RING - 1;
+                if (pf < BPB)
+                    issue(ring[pf % RING], jc, pf);
+                else
+                    issue(ring[pf % RING], jn, pf - BPB);
+            }
+            // use batch bb
+            float sv[U];
+            int sidx[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int t = bb * U + u;
+                sv[u] = __shfl_sync(0xffffffffu, sc[t / G], tbase + (t % G));
+                sidx[u] = NZ ? __shfl_sync(0xffffffffu, ic[t / G], tbase + (t % G)) : 0;
+            }
+            float2 y2[U][E2];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int v = 0; v < VPL; ++v)
+                    unpack2<T>(ring[bb % RING][u][v], &y2[u][v * W2]);
+            if constexpr (MODE == M_SPMM) {
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const float2 c2 = make_float2(sv[u], sv[u]);
+#pragma unroll
+                    for (int e = 0; e < E2; ++e)
+                        acc2[e] = ffma2(c2, y2[u][e], acc2[e]);
+                }
+            } else {
+                float d[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    float2 t2 = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int e = 0; e < E2; ++e)
+                        t2 = ffma2(l2[e], y2[u][e], t2);
+                    d[u] = t2.x + t2.y;
+                }
+                // sum over the G lanes of the group, two dot products per step
+#pragma unroll
+                for (int off = G / 2; off > 0; off >>= 1) {
+#pragma unroll
+                    for (int u = 0; u + 1 < U; u += 2) {
+                        const float2 o = make_float2(__shfl_xor_sync(0xffffffffu, d[u], off),
+                                                     __shfl_xor_sync(0xffffffffu, d[u + 1], off));
+                        const float2 s2 = fadd2(make_float2(d[u], d[u + 1]), o);
+                        d[u] = s2.x;
+                        d[u + 1] = s2.y;
+                    }
+                    if constexpr (U % 2)
+                        d[U - 1] += __shfl_xor_sync(0xffffffffu, d[U - 1], off);
+                }
+                if constexpr (MODE == M_FUSED) {
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const float c = sv[u] * d[u];
+                        const float2 c2 = make_float2(c, c);
+#pragma unroll
+                        for (int e = 0; e < E2; ++e)
+                            acc2[e] = ffma2(c2, y2[u][e], acc2[e]);
+                    }
+                } else {   // M_SDDMM
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+                        if (sidx[u] >= 0 && lig == (u % G))
+                            a.nzout[sidx[u]] = sv[u] * d[u];
+                }
+            }
+        }
+        // the next block becomes current; fetch the one after it
+#pragma unroll
+        for (int e = 0; e < K; ++e) {
+            jc[e] = jn[e]; sc[e] = sn[e]; ic[e] = in_[e];
+        }
+        load_block(bk + 2, jn, sn, in_);
+    }
+
+    if constexpr (ACC) {
+        if (active) {
+            float *dst = slot >= 0 ? a.partials + (size_t)slot * R
+                                   : (a.out ? a.out + (size_t)row * R : nullptr);
+            if (dst) {
+#pragma unroll
+                for (int v = 0; v < VPL; ++v) {
+#pragma unroll
+                    for (int w = 0; w < W2; w += 2) {
+                        const int k = (v * G + lig) * EPV + 2 * w;
+                        const float2 p0 = acc2[v * W2 + w], p1 = acc2[v * W2 + w + 1];
+                        ld.st4(dst + k, make_float4(p0.x, p0.y, p1.x, p1.y));
+                    }
+                }
+            }
+        }
+    }
+}
+
+template <int MODE, typename T, int R, int VPL, int U, int RING>
+cudaError_t launch_pipe(const PassArgs &a, cudaStream_t st)
+{
+    constexpr int G = TeamShape<T, R, VPL, 1>::G;
+    const long long total = (long long)a.n_chunks + a.n_light;
+    const long long blocks = (total * G + 255) / 256;
+    pipe_pass_kernel<MODE, T, R, VPL, U, RING><<<(unsigned)blocks, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+// Whether (VPL, U, RING) fits rows of R elements of T: a valid team layout
+// whose index block holds a whole number of rings of batches.
+template <typename T, int R>
+constexpr bool pipe_ok(int V, int U, int RING)
+{
+    if (!team_ok<T, R>(V, 1))
+        return false;
+    const int g = R * (int)sizeof(T) / 16 / V;
+    const int ib = (g >= 8 ? 1 : 8 / g) * g;
+    return ib % (U * RING) == 0;
+}
+
+// Variants: (VPL, U, RING) with VPL as a multiple of the row shape's minimum.
+template <typename T, int R>
+cudaError_t dispatch_pipe(int mode, int vpl, int u, int ring, const PassArgs &a, cudaStream_t st)
+{
+    constexpr int B = base_vpl<T, R>();
+#define FMM_PIPE(M, V, UU, RR)                                                     \
+    if constexpr (pipe_ok<T, R>(V, UU, RR))                                        \
+        if (mode == M && vpl == V && u == UU && ring == RR)                        \
+            return launch_pipe<M, T, R, V, UU, RR>(a, st);
+#define FMM_PIPE_MODES(V, UU, RR) \
+    FMM_PIPE(M_FUSED, V, UU, RR) FMM_PIPE(M_SDDMM, V, UU, RR) FMM_PIPE(M_SPMM, V, UU, RR)
+    FMM_PIPE_MODES(B, 2, 2)
+    FMM_PIPE_MODES(B, 2, 4)
+    FMM_PIPE_MODES(B, 1, 2)
+    FMM_PIPE_MODES(B, 1, 4)
+    FMM_PIPE_MODES(2 * B, 2, 2)
+    FMM_PIPE_MODES(2 * B, 1, 2)
+#undef FMM_PIPE_MODES
+#undef FMM_PIPE
+    return cudaErrorNotSupported;   // not instantiated for this width: the caller falls back
+}
+
+template <typename T>
+cudaError_t launch_pipe_typed(int mode, int vpl_mult, int u, int ring, const PassArgs &a,
+                              cudaStream_t st)
+{
+    if ((long long)a.n_chunks + a.n_light == 0)
+        return cudaSuccess;
+    switch (a.r) {
+    case 32: return dispatch_pipe<T, 32>(mode, vpl_mult * base_vpl<T, 32>(), u, ring, a, st);
+    case 64: return dispatch_pipe<T, 64>(mode, vpl_mult * base_vpl<T, 64>(), u, ring, a, st);
+    case 128: return dispatch_pipe<T, 128>(mode, vpl_mult * base_vpl<T, 128>(), u, ring, a, st);
+    case 256: return dispatch_pipe<T, 256>(mode, vpl_mult * base_vpl<T, 256>(), u, ring, a, st);
+    default: return cudaErrorNotSupported;
+    }
+}
+
+}  // namespace fmm

@@ -1,0 +1,10 @@
+// float32 instantiations of the pipelined forward-role row passes.
+#include "fmm_pipe.cuh"
+
+namespace fmm {
+cudaError_t launch_pipe_f32(int mode, int vpl_mult, int u, int ring, const PassArgs &a,
+                            cudaStream_t st)
+{
+    return launch_pipe_typed<float>(mode, vpl_mult, u, ring, a, st);
+}
+}  // namespace fmm

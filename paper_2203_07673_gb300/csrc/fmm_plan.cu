@@ -441,7 +441,7 @@ int validate_csr(const fmm_csr *S, cudaStream_t st, int64_t *first_bad)
     cudaError_t e = cudaMemcpyAsync(d_bad, init, sizeof(init), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) {
         const int64_t work = std::max<int64_t>((int64_t)S->m + 1, S->nnz);
-        validate_kernel<<<blocks_for(work, 256, 152 * 16), 256, 0, st>>>(
+        validate_kernel<<<blocks_for(work, 256, sm_count() * 16), 256, 0, st>>>(
             S->row_ptr, S->col_idx, S->m, S->n, S->nnz, d_bad, d_bad + 1);
         e = cudaGetLastError();
     }
@@ -526,9 +526,9 @@ int create_plan(const fmm_csr *S, int32_t r, int32_t dtype, const fmm_plan_optio
         uint32_t *cnt = reinterpret_cast<uint32_t *>(p->row_ptr_t);
         PLAN_TRY(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * ((size_t)S->n + 1), st), "memset");
         if (S->nnz > 0) {
-            count_cols_kernel<<<blocks_for(S->nnz, 256, 152 * 32), 256, 0, st>>>(S->col_idx,
+            count_cols_kernel<<<blocks_for(S->nnz, 256, sm_count() * 32), 256, 0, st>>>(S->col_idx,
                                                                                  S->nnz, cnt);
-            init_pairs_kernel<<<blocks_for(S->nnz, 256, 152 * 32), 256, 0, st>>>(
+            init_pairs_kernel<<<blocks_for(S->nnz, 256, sm_count() * 32), 256, 0, st>>>(
                 S->col_idx, S->nnz, tmp.ka, tmp.va);
             PLAN_TRY(cudaGetLastError(), "transpose setup");
         }
@@ -543,7 +543,7 @@ int create_plan(const fmm_csr *S, int32_t r, int32_t dtype, const fmm_plan_optio
             PLAN_TRY(cudaMemcpyAsync(p->perm_t, in_b ? tmp.vb : tmp.va,
                                      sizeof(int32_t) * (size_t)S->nnz, cudaMemcpyDeviceToDevice, st),
                      "copy perm");
-            rows_of_kernel<<<blocks_for(S->nnz, 256, 152 * 32), 256, 0, st>>>(
+            rows_of_kernel<<<blocks_for(S->nnz, 256, sm_count() * 32), 256, 0, st>>>(
                 S->row_ptr, S->m, p->perm_t, p->col_idx_t, S->nnz);
             PLAN_TRY(cudaGetLastError(), "transpose rows");
         }
@@ -605,12 +605,7 @@ int32_t default_split_nnz(int64_t nnz, int32_t r, int32_t dtype, const KernelVar
         const int vpl = (vecs > 32 ? vecs / 32 : 1) * v.vpl_mult;
         lanes = std::min(32, std::max(1, vecs / std::max(1, vpl)) * std::max(1, v.ng));
     }
-    int sms = 0, dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        sms <= 0)
-        sms = 152;
-    const int64_t teams = (int64_t)sms * 32 * (32 / lanes);
+    const int64_t teams = (int64_t)sm_count() * 32 * (32 / lanes);
     return (int32_t)std::min<int64_t>(8192, std::max<int64_t>(256, nnz / (4 * teams)));
 }
 

@@ -47,6 +47,7 @@ _SIGNATURES = {
     "fmm_batch_forward": ([_P, _P], ctypes.c_int),
     "fmm_batch_backward": ([_P, _P], ctypes.c_int),
     "fmm_batch_destroy": ([_P], ctypes.c_int),
+    "fmm_probe_gather": ([_P, ctypes.c_int64, _I32, _P, ctypes.c_int64, _P, _P], ctypes.c_int),
     "fmm_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "fmm_last_error": ([], ctypes.c_char_p),
     "fmm_version": ([], ctypes.c_int32),
@@ -308,21 +309,51 @@ def fusedmm_t_bwd(plan: Plan, vals, A, B, Gn, need=(True, True, True), stream=No
 def fusedmm_noalloc(row_ptr, col_idx, n: int, vals, A, B, out=None, stream=None):
     """fmm_fusedmm_noalloc: FusedMMA from the CSR directly, with no plan and
     no device allocation inside the library (``out`` is allocated here by
-    torch if not given).  Calls that overlap on the GPU must not be issued:
+    torch if not given).  Every tensor must be on A's device, which is made
+    current for the call.  Calls that overlap on the GPU must not be issued:
     they share one fixed scratch array."""
+    if not isinstance(A, torch.Tensor) or A.dim() != 2:
+        raise ValueError("A must be a 2-D tensor (m x r)")
     dt = _DT.get(A.dtype)
     if dt is None:
         raise TypeError(f"unsupported dtype {A.dtype}")
+    dev = A.device
     m, r = A.shape
+    if not isinstance(row_ptr, torch.Tensor) or row_ptr.dim() != 1 or row_ptr.numel() != m + 1:
+        raise ValueError(f"row_ptr must be 1-D with m + 1 = {m + 1} entries")
+    if not isinstance(col_idx, torch.Tensor) or col_idx.dim() != 1:
+        raise ValueError("col_idx must be 1-D")
+    nnz = col_idx.numel()
     if out is None:
-        out = torch.empty((m, r), dtype=torch.float32, device=A.device)
-    csr = _Csr(m, int(n), col_idx.numel(), _ptr(row_ptr, "row_ptr", torch.int32),
-               _ptr(col_idx, "col_idx", torch.int32))
-    rc = lib().fmm_fusedmm_noalloc(ctypes.byref(csr), int(r), dt, _ptr(vals, "vals", torch.float32),
-                                   _ptr(A, "A"), _ptr(B, "B", A.dtype),
-                                   _ptr(out, "out", torch.float32, (m, r)), _stream(stream))
+        out = torch.empty((m, r), dtype=torch.float32, device=dev)
+    csr = _Csr(m, int(n), nnz, _ptr(row_ptr, "row_ptr", torch.int32, device=dev),
+               _ptr(col_idx, "col_idx", torch.int32, device=dev))
+    args = (_ptr(vals, "vals", torch.float32, (nnz,), device=dev),
+            _ptr(A, "A", device=dev), _ptr(B, "B", A.dtype, (int(n), r), device=dev),
+            _ptr(out, "out", torch.float32, (m, r), device=dev))
+    with torch.cuda.device(dev):
+        rc = lib().fmm_fusedmm_noalloc(ctypes.byref(csr), int(r), dt, *args, _stream(stream))
     _check(rc, "fmm_fusedmm_noalloc")
     return out
+
+
+def probe_gather(table, idx, sink=None, stream=None):
+    """fmm_probe_gather: fetch table[idx[k]] for every k and nothing else (a
+    measurement aid: the gather ceiling of a pass walking idx).  table is a
+    2-D contiguous CUDA tensor whose rows are 64, 128, 256 or 512 bytes;
+    idx int32 on the same device."""
+    if not isinstance(table, torch.Tensor) or table.dim() != 2:
+        raise ValueError("table must be a 2-D tensor")
+    dev = table.device
+    row_bytes = table.shape[1] * table.element_size()
+    if sink is None:
+        sink = torch.zeros(1, dtype=torch.int32, device=dev)
+    args = (_ptr(table, "table", device=dev), table.shape[0], row_bytes,
+            _ptr(idx, "idx", torch.int32, device=dev), idx.numel(),
+            _ptr(sink, "sink", device=dev))
+    with torch.cuda.device(dev):
+        rc = lib().fmm_probe_gather(*args, _stream(stream))
+    _check(rc, "fmm_probe_gather")
 
 
 class _BatchItem(ctypes.Structure):

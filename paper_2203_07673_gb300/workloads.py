@@ -407,3 +407,80 @@ def batched_matrix_torch(spec: dict, t: int, device, seed_index: int = 5) -> dic
     A = torch.randn(rows, r, generator=g, device=device) * std
     B = torch.randn(rows, r, generator=g, device=device) * std
     return dict(row_ptr=rp, col_idx=ci, vals=vals, A=A, B=B, r=r, m=rows, n=rows)
+
+
+# ---------------------------------------------------------------------------
+# The Zipf-row workload (workload 4's recipe) drawn with torch on a device:
+# the 80M-nonzero pattern in seconds instead of a minute on the host.  Same
+# recipe as zipf_rows / workload(4), another random stream.
+
+def zipf_degrees_torch(m, total_nnz, alpha, dmax, g, device, n=None):
+    """Row degrees clip(round(c * w_i), 1, min(dmax, n)), w_i ~ Zipf(alpha)
+    truncated to [1, dmax], c by bisection so that the sum is within 0.1 %
+    of total_nnz (torch.round: ties to even, as np.round)."""
+    import torch
+    k = torch.arange(1, dmax + 1, dtype=torch.float64, device=device)
+    cdf = torch.cumsum(k ** (-alpha), 0)
+    cdf /= cdf[-1].clone()
+    u = torch.rand(m, generator=g, device=device, dtype=torch.float64)
+    w = torch.clamp(torch.searchsorted(cdf, u, right=True) + 1, max=dmax).double()
+    cap = dmax if n is None else min(dmax, n)
+
+    def degs(c):
+        return torch.clamp(torch.round(c * w), 1, cap).long()
+
+    lo, hi = 0.0, float(cap)
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        s = int(degs(mid).sum())
+        if abs(s - total_nnz) <= 0.001 * total_nnz:
+            return degs(mid)
+        if s < total_nnz:
+            lo = mid
+        else:
+            hi = mid
+    return degs(0.5 * (lo + hi))
+
+
+def zipf_rows_torch(m, n, total_nnz, alpha, dmax, g, device):
+    """Device (row_ptr, col_idx) int32 of an m x n pattern with Zipf row
+    degrees and uniform distinct columns, sorted within each row."""
+    import torch
+    d = zipf_degrees_torch(m, total_nnz, alpha, dmax, g, device, n=n)
+    rows = torch.repeat_interleave(torch.arange(m, device=device, dtype=torch.int64), d)
+    cols = torch.randint(0, n, rows.shape, generator=g, device=device, dtype=torch.int64)
+    while True:
+        keys, order = torch.sort(rows * n + cols)
+        rows = rows[order]
+        dup = torch.zeros_like(keys, dtype=torch.bool)
+        if keys.numel() > 1:
+            dup[1:] = keys[1:] == keys[:-1]
+        nd = int(dup.sum())
+        cols = keys % n
+        if nd == 0:
+            break
+        cols[dup] = torch.randint(0, n, (nd,), generator=g, device=device, dtype=torch.int64)
+    del keys, order, dup
+    counts = torch.bincount(rows, minlength=m)
+    row_ptr = torch.zeros(m + 1, dtype=torch.int64, device=device)
+    row_ptr[1:] = torch.cumsum(counts, 0)
+    return row_ptr.int(), cols.int()
+
+
+def zipf_workload_torch(device, scale_rows: float = 1.0, seed_index: int = 4) -> dict:
+    """Workload 4 as device tensors: 2^21 x 2^19 (times scale_rows) Zipf(1.2)
+    rows in [1, 4096] with 80M nonzeros, s in {1, 1.5, ..., 5}, A, B ~
+    N(0, 0.1) float32, r = 64."""
+    import torch
+    g = _torch_gen(device, (ROOT_SEED + seed_index) * 1000003 + 77)
+    m = max(1, int((1 << 21) * scale_rows))
+    n = max(1, int((1 << 19) * scale_rows))
+    total = max(m, int(80_000_000 * scale_rows))
+    rp, ci = zipf_rows_torch(m, n, total, 1.2, 4096, g, device)
+    nnz = ci.numel()
+    vals = torch.round((torch.rand(nnz, generator=g, device=device) * 4.0 + 1.0) * 2.0) / 2.0
+    std = math.sqrt(0.1)
+    A = torch.randn(m, 64, generator=g, device=device) * std
+    B = torch.randn(n, 64, generator=g, device=device) * std
+    return dict(row_ptr=rp, col_idx=ci, vals=vals, A=A, B=B, r=64, m=m, n=n,
+                name=WORKLOADS[4] + " [drawn on the device]")

@@ -6,13 +6,16 @@ allocation on its hot path); they cannot create a plan, because plan creation
 allocates.  This entry point takes the CSR directly and keeps its only scratch
 (chunk list and partial rows of long rows) in a fixed file-scope device array.
 
-The test calls it through the C ABI, twice in a row on the same inputs and
-once more on a different pattern, and checks each result against the plan
-path (fmm_fusedmm) with the tolerance the parity tests use.  The patterns
-include rows longer than the chunk size, so the scratch array is exercised,
-and the second call checks that state left by the first is cleared.
-This file sorts last so that a run stopping at the first failure has already
-run every other test.
+The tests call it through the C ABI and through the Python wrapper, twice in a
+row on the same inputs and once more on a different pattern, and check every
+element of each result against the FP64 oracle with the rounding bound of
+the parity tests (and against the plan path, fmm_fusedmm, with twice that
+bound).  The patterns include rows longer than the chunk size, so the scratch
+array is exercised, and the repeated call checks that state left by the
+first is cleared.  One pattern is large enough (11.8M nonzeros at r = 256)
+that the chunk size grows past its 512 minimum to keep every chunk inside
+the fixed array.  This file sorts last so that a run stopping at the first
+failure has already run every other test.
 """
 import ctypes
 
@@ -21,7 +24,7 @@ import pytest
 import torch
 
 import oracle
-from parity_utils import U32, relF, upload
+from parity_utils import U32, assert_close, host64, relF, rows_problem, upload
 from paper_2203_07673_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -56,7 +59,7 @@ def _close_to_plan_path(name, got, ref, mag, r, deg):
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16], ids=["f32", "bf16"])
 @pytest.mark.parametrize("r", [64, 128, 24])
-def test_noalloc_matches_plan_path_on_two_calls(r, dtype):
+def test_noalloc_matches_oracle_on_two_calls(r, dtype):
     from paper_2203_07673_gb300 import fmm
     code = fmm.FMM_F32 if dtype == torch.float32 else fmm.FMM_BF16
     results = []
@@ -67,19 +70,73 @@ def test_noalloc_matches_plan_path_on_two_calls(r, dtype):
         A = (rng.standard_normal((S.m, r)) / np.sqrt(r)).astype(np.float32)
         B = (rng.standard_normal((S.n, r)) / np.sqrt(r)).astype(np.float32)
         rp, ci, vt, At, Bt = upload(S, vals, A, B, dtype)
-        plan = fmm.Plan(rp, ci, S.n, r, dtype)
-        ref = fmm.fusedmm(plan, vt, At, Bt)
         out = torch.full((S.m, r), float("nan"), device="cuda")
         _noalloc(fmm, S, rp, ci, r, code, vt, At, Bt, out)
         torch.cuda.synchronize()
-        mag = oracle.fusedmm(S.row_ptr, S.col_idx, vals, np.abs(At.double().cpu().numpy()),
-                             np.abs(Bt.double().cpu().numpy()), S.n)
+        # the oracle on exactly the values the GPU received (bf16 widened)
+        A64, B64 = host64(At), host64(Bt)
+        exp = oracle.fusedmm(S.row_ptr, S.col_idx, vals, A64, B64, S.n)
+        mag = oracle.fusedmm(S.row_ptr, S.col_idx, vals, np.abs(A64), np.abs(B64), S.n)
         deg = int(S.degrees().max())
-        _close_to_plan_path(f"noalloc seed {seed}", out, ref, mag, r, deg)
+        assert_close(f"noalloc seed {seed}", out, exp, mag, r, deg)
+        # and the plan path on the same inputs
+        plan = fmm.Plan(rp, ci, S.n, r, dtype)
+        ref = fmm.fusedmm(plan, vt, At, Bt)
+        _close_to_plan_path(f"noalloc vs plan seed {seed}", out, ref, mag, r, deg)
         results.append(out.clone())
         plan.close()
     # the same inputs give the same bits on the repeated call
     assert torch.equal(results[0], results[1])
+
+
+def test_noalloc_wrapper_chunk_size_above_minimum():
+    """Through fmm.fusedmm_noalloc: 2^17 rows of about 90 nonzeros plus hub
+    rows of 3000 and 5000 at r = 256, so the chunk size is
+    ch = ceil(2 nnz / (8 Mi / r)) > 512; sampled rows (the hub rows among
+    them) against the oracle, and a repeated call bit for bit."""
+    from paper_2203_07673_gb300 import fmm
+    r, m, n = 256, 1 << 17, 1 << 16
+    rng = np.random.default_rng(77)
+    S = wl.random_csr(m, n, rng, mean_deg=90, empty_frac=0.02,
+                      hubs=((5, 3000), (70000, 5000), (m - 1, 3000)))
+    cap = min(1 << 16, (1 << 23) // r)
+    ch = max(512, -(-2 * S.nnz // cap))
+    assert ch > 512 and S.degrees().max() > ch
+    vals = rng.uniform(0, 1, S.nnz).astype(np.float32)
+    A = wl.normal(m, r, 1.0 / r, rng)
+    B = wl.normal(n, r, 1.0 / r, rng)
+    rp, ci, vt, At, Bt = upload(S, vals, A, B)
+    out1 = fmm.fusedmm_noalloc(rp, ci, n, vt, At, Bt)
+    out2 = torch.full_like(out1, float("nan"))
+    fmm.fusedmm_noalloc(rp, ci, n, vt, At, Bt, out=out2)
+    torch.cuda.synchronize()
+    assert torch.equal(out1, out2)
+    rows = np.unique(np.concatenate([[5, 70000, m - 1],
+                                     np.random.default_rng(3).choice(m, 64, replace=False)]))
+    sub_rp, sub_ci, sub_v, cols, _ = rows_problem(S, rows, vals)
+    exp = oracle.fusedmm(sub_rp, sub_ci, sub_v, A[rows], B[cols], len(cols))
+    mag = oracle.fusedmm(sub_rp, sub_ci, sub_v, np.abs(A[rows]), np.abs(B[cols]), len(cols))
+    deg = int(S.degrees()[rows].max())
+    assert_close("noalloc r=256 sampled rows", out1[torch.from_numpy(rows).cuda()], exp, mag, r,
+                 deg)
+
+
+def test_noalloc_wrapper_checks_its_arguments():
+    from paper_2203_07673_gb300 import fmm
+    S = _pattern(3)
+    r = 32
+    rng = np.random.default_rng(4)
+    A = rng.standard_normal((S.m, r)).astype(np.float32)
+    B = rng.standard_normal((S.n, r)).astype(np.float32)
+    rp, ci, vt, At, Bt = upload(S, None, A, B)
+    with pytest.raises(ValueError):
+        fmm.fusedmm_noalloc(rp[:-1], ci, S.n, None, At, Bt)        # row_ptr too short
+    with pytest.raises(ValueError):
+        fmm.fusedmm_noalloc(rp, ci, S.n, None, At, Bt[:-1])        # B has n - 1 rows
+    with pytest.raises(ValueError):
+        fmm.fusedmm_noalloc(rp, ci, S.n, torch.ones(S.nnz - 1, device="cuda"), At, Bt)
+    with pytest.raises(TypeError):
+        fmm.fusedmm_noalloc(rp, ci, S.n, None, At, Bt.to(torch.bfloat16))
 
 
 def test_noalloc_rejects_oversized_r():
