@@ -1271,6 +1271,8 @@ def main():
                     help="keep nvidia-smi's raw clock samples under this path prefix")
     ap.add_argument("--no-zipf", action="store_true",
                     help="default workload without the Zipf-row (c4) section")
+    ap.add_argument("--zipf-only", action="store_true",
+                    help="only the Zipf-row (c4) section, printed as one JSON object")
     ap.add_argument("--no-library", action="store_true",
                     help="skip the cuSPARSE (torch.sparse) comparison")
     args = ap.parse_args()
@@ -1287,7 +1289,15 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    if args.als:
+    if args.zipf_only:
+        import torch
+        dev = torch.device("cuda", local_rank)
+        torch.cuda.set_device(dev)
+        res = zipf_section(args, dev, torch.cuda.current_stream())
+        if rank == 0:
+            print(json.dumps(res), flush=True)
+        rc = 0
+    elif args.als:
         rc = run_als(args, rank, world, local_rank)
     elif args.gat:
         rc = run_gat(args, rank, world, local_rank)

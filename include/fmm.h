@@ -70,7 +70,9 @@ enum fmm_status {
     FMM_EUNSUPPORTED = -2,  /* unknown dtype, r < 1, or a missing S^T       */
     FMM_EOVERFLOW = -3,     /* nnz >= 2^31 or a size that overflows         */
     FMM_ECUDA = -4,         /* CUDA runtime error (launch, copy, device)    */
-    FMM_ENOMEM = -5         /* device allocation failed (plan creation)     */
+    FMM_ENOMEM = -5,        /* device allocation failed (plan creation)     */
+    FMM_ETIMEOUT = -6       /* a kernel gave up a bounded wait (see
+                               fmm_plan_status)                             */
 };
 
 enum fmm_dtype {
@@ -111,8 +113,28 @@ typedef struct fmm_plan_options {
                                  falls back to 118); or 1000 + D*10 + V
                                  (1041, 1042, 1081, 1082): FusedMM, SDDMM
                                  and SpMM stage the next D - 1 gathered rows
-                                 of each row in shared memory (cp.async),
-                                 the backward passes use V*100 + 12          */
+                                 of each row in shared memory (cp.async);
+                                 or F*10000 + M*1000 + P*100 + U*10 + V
+                                 (22212, 23212, 22412, 32212, 24221, 34221,
+                                 23421, 23241): FusedMM, SDDMM and SpMM keep
+                                 the gathered rows of the next P - 1 (F = 2)
+                                 or P (F = 3) batches of U nonzeros in
+                                 flight in registers, with M resident
+                                 256-thread blocks per SM asked for; or
+                                 40000 + M*1000 + D*10 + V (44042, 43082,
+                                 44041, 44081): FusedMM, SDDMM and SpMM copy
+                                 each gathered row into a ring of D slots
+                                 in shared memory with one bulk copy
+                                 (cp.async.bulk, mbarrier completion), M
+                                 resident blocks per SM.  With these last
+                                 three kinds the backward passes run the
+                                 width's default team layout (112 for
+                                 bfloat16 rows, 212 for float32 rows of at
+                                 most 32 vectors).  A layout a width does
+                                 not have falls back to that team layout.
+                                 Default: 32212 for bfloat16 rows of r = 64
+                                 and 128, 1042 for float32 rows of r = 128,
+                                 else that team layout                       */
 } fmm_plan_options;
 
 typedef struct fmm_plan fmm_plan;   /* opaque */
@@ -170,6 +192,17 @@ int fmm_plan_set_values(fmm_plan *plan, const float *vals, fmm_stream stream);
 /* Frees a plan and its workspace (synchronises the device first).  NULL is a
  * no-op. */
 int fmm_plan_destroy(fmm_plan *plan);
+
+/*
+ * Reports and clears the plan's device error word.  Synchronises the stream.
+ * Returns FMM_OK, or FMM_ETIMEOUT if a pass of the plan queued before this
+ * call gave up waiting for a gathered row to arrive in shared memory (the
+ * bulk-staged kernel variants bound every wait; after giving up, the rest
+ * of that pass's rows on the affected warp are treated as zeros, so its
+ * outputs are wrong).  Status of earlier calls only: compute calls return
+ * before their kernels run.
+ */
+int fmm_plan_status(fmm_plan *plan, fmm_stream stream);
 
 /* Copies the plan's sizes and schedule summary into *info. */
 int fmm_plan_get_info(const fmm_plan *plan, fmm_plan_info *info);

@@ -35,13 +35,17 @@ static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 
 // nonzeros per group per batch (the combinations instantiated in
 // fmm_rows.cuh; a combination that does not fit a row shape falls back to
 // the shape's default); 1000 + ring depth * 10 + vectors-per-lane multiple
-// for the staged pass (fmm_staged.cuh); 2000 + register-ring batches * 100 +
-// nonzeros per batch * 10 + vectors-per-lane multiple for the pipelined pass
-// (fmm_pipe.cuh).  The backward roles of staged and pipelined codes run the
-// team kernel with one group per row and 2 nonzeros per batch.
+// for the staged pass (fmm_staged.cuh); (2 + refill) * 10000 + resident
+// blocks per SM * 1000 + register-ring batches * 100 + nonzeros per batch *
+// 10 + vectors-per-lane multiple for the pipelined pass (fmm_pipe.cuh);
+// 40000 + resident blocks per SM * 1000 + ring slots * 10 + vectors-per-lane
+// multiple for the bulk-staged pass (fmm_bulk.cuh).  The
+// backward roles of staged, pipelined and bulk-staged codes run the team
+// kernel in the width's default layout (team_default_variant).
 static const int kVariantCodes[] = {114, 118, 222, 224, 441, 442, 214, 124, 112, 122, 212, 221,
                                     1041, 1042, 1081, 1082,
-                                    2221, 2421, 2211, 2411, 2222, 2212};
+                                    22212, 23212, 22412, 32212, 24221, 34221, 23421, 23241,
+                                    44042, 43082, 44041, 44081};
 
 bool variant_known(int code)
 {
@@ -53,7 +57,17 @@ bool variant_known(int code)
 KernelVariant decode_variant(int code)
 {
     KernelVariant v;
-    if (code >= 2000) {
+    if (code >= 40000) {
+        v.mb = (code / 1000) % 10;
+        v.depth = (code / 10) % 100;
+        v.vpl_mult = code % 10;
+        v.ng = 1;
+        v.u = 2;
+        return v;
+    }
+    if (code >= 20000) {
+        v.refill = code / 10000 - 2;
+        v.mb = (code / 1000) % 10;
         v.ring = (code / 100) % 10;
         v.u = (code / 10) % 10;
         v.vpl_mult = code % 10;
@@ -75,8 +89,10 @@ KernelVariant decode_variant(int code)
 
 int encode_variant(const KernelVariant &v)
 {
+    if (v.depth > 0)
+        return 40000 + v.mb * 1000 + v.depth * 10 + v.vpl_mult;
     if (v.ring > 0)
-        return 2000 + v.ring * 100 + v.u * 10 + v.vpl_mult;
+        return (2 + v.refill) * 10000 + v.mb * 1000 + v.ring * 100 + v.u * 10 + v.vpl_mult;
     if (v.stages > 0)
         return 1000 + v.stages * 10 + v.vpl_mult;
     return v.vpl_mult * 100 + v.ng * 10 + v.u;
@@ -92,19 +108,28 @@ cudaError_t launch_pass(int mode, int dtype, const KernelVariant &v, const PassA
         return dtype == FMM_BF16 ? launch_staged_bf16(mode, v.vpl_mult, v.stages, a, st)
                                  : launch_staged_f32(mode, v.vpl_mult, v.stages, a, st);
     }
+    if (v.depth > 0 && vec && fwd) {
+        const cudaError_t e = dtype == FMM_BF16
+                                  ? launch_bulk_bf16(mode, v.vpl_mult, v.depth, v.mb, a, st)
+                                  : launch_bulk_f32(mode, v.vpl_mult, v.depth, v.mb, a, st);
+        if (e != cudaErrorNotSupported)
+            return e;
+    }
     if (v.ring > 0 && vec && fwd) {
         const cudaError_t e = dtype == FMM_BF16
-                                  ? launch_pipe_bf16(mode, v.vpl_mult, v.u, v.ring, a, st)
-                                  : launch_pipe_f32(mode, v.vpl_mult, v.u, v.ring, a, st);
+                                  ? launch_pipe_bf16(mode, v.vpl_mult, v.u, v.ring, v.mb, v.refill, a, st)
+                                  : launch_pipe_f32(mode, v.vpl_mult, v.u, v.ring, v.mb, v.refill, a, st);
         if (e != cudaErrorNotSupported)
             return e;
         // a ring layout this width does not have: the team kernel below
     }
-    // backward roles of a staged or pipelined plan: one group, 2 per batch
-    const int u = (v.stages > 0 || v.ring > 0) ? 2 : v.u;
+    // backward roles of a staged, pipelined or bulk-staged plan: the team
+    // kernel's default layout for the width
+    const KernelVariant t =
+        (v.stages > 0 || v.ring > 0 || v.depth > 0) ? team_default_variant(a.r, dtype) : v;
     if (dtype == FMM_BF16)
-        return launch_pass_bf16(mode, v.vpl_mult, v.ng, u, vec, a, st);
-    return launch_pass_f32(mode, v.vpl_mult, v.ng, u, vec, a, st);
+        return launch_pass_bf16(mode, t.vpl_mult, t.ng, t.u, vec, a, st);
+    return launch_pass_f32(mode, t.vpl_mult, t.ng, t.u, vec, a, st);
 }
 
 }  // namespace fmm
@@ -173,6 +198,7 @@ int run_pass(const fmm_plan *p, const Side &side, int mode, const float *s, cons
     a.out = out;
     a.nzout = nzout;
     a.r = p->r;
+    a.err = p->err;
     cudaError_t e = cudaSuccess;
     if (side.perm && s) {
         if (s == p->static_src && p->vals_static) {
@@ -390,6 +416,27 @@ int fmm_fusedmm_t_bwd(const fmm_plan *p, const float *vals, const void *A, const
     return FMM_OK;
 }
 
+int fmm_plan_status(fmm_plan *p, fmm_stream stream)
+{
+    CHECK(check_plan(p));
+    int32_t flag = 0;
+    cudaError_t e = cudaMemcpyAsync(&flag, p->err, sizeof(flag), cudaMemcpyDeviceToHost,
+                                    (cudaStream_t)stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e == cudaSuccess && flag)
+        e = cudaMemsetAsync(p->err, 0, sizeof(int32_t), (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        set_error("fmm_plan_status", e);
+        return FMM_ECUDA;
+    }
+    if (flag) {
+        set_error_msg("a row pass gave up waiting for a gathered row copy");
+        return FMM_ETIMEOUT;
+    }
+    return FMM_OK;
+}
+
 const char *fmm_status_string(int status)
 {
     switch (status) {
@@ -399,6 +446,7 @@ const char *fmm_status_string(int status)
     case FMM_EOVERFLOW: return "size overflow";
     case FMM_ECUDA: return "CUDA error";
     case FMM_ENOMEM: return "out of device memory";
+    case FMM_ETIMEOUT: return "a bounded wait gave up";
     default: return "unknown status";
     }
 }

@@ -159,9 +159,7 @@ int batch_code(int dtype, int mode, int r, const KernelVariant &v)
         return want;
     // the default team layout of the width (the batch kernels run the team
     // pass only), with fewer nonzeros per batch if needed
-    KernelVariant d = default_variant(r, dtype, 0.0);
-    d.stages = 0;
-    d.ring = 0;
+    KernelVariant d = team_default_variant(r, dtype);
     for (int u : {d.u, 2, 1}) {
         d.u = u;
         const int c = encode_variant(d);

@@ -18,6 +18,10 @@ struct KernelVariant {
     int stages = 0;   // > 0: the staged pass (fmm_staged.cuh) with this ring depth
     int ring = 0;     // > 0: the pipelined pass (fmm_pipe.cuh), this many batches in
                       // the register ring (forward roles; u nonzeros per batch)
+    int mb = 0;       // pipelined pass: resident 256-thread blocks per SM asked for
+    int refill = 0;   // pipelined pass: 1 = refill a slot as soon as it is read
+    int depth = 0;    // > 0: the bulk-staged pass (fmm_bulk.cuh), this many row
+                      // slots in shared memory per team (forward roles)
 };
 
 // One side of a plan: the CSR that a row pass walks (S itself, or S^T with a
@@ -100,6 +104,8 @@ struct PassArgs {
     float *out;                // rows x r (NULL: not stored)
     float *nzout;              // per-nonzero output in S order (NULL: none)
     int32_t r;
+    int32_t *err;              // device word set to 1 by a pass that gave up a
+                               // bounded wait (NULL: not reported)
 };
 
 // Launches one row pass (main kernel; the combine kernel for split rows is
@@ -118,10 +124,16 @@ cudaError_t launch_staged_bf16(int mode, int vpl_mult, int stages, const PassArg
                                cudaStream_t st);
 // Pipelined forward-role passes (fmm_pipe.cuh): FusedMM, SDDMM and SpMM with
 // a register ring of `ring` batches of u gathered rows per team; vector path.
-cudaError_t launch_pipe_f32(int mode, int vpl_mult, int u, int ring, const PassArgs &a,
+// Bulk-staged forward-role passes (fmm_bulk.cuh): rows copied into a
+// shared-memory ring of `depth` slots per team by cp.async.bulk.
+cudaError_t launch_bulk_f32(int mode, int vpl_mult, int depth, int mb, const PassArgs &a,
                             cudaStream_t st);
-cudaError_t launch_pipe_bf16(int mode, int vpl_mult, int u, int ring, const PassArgs &a,
+cudaError_t launch_bulk_bf16(int mode, int vpl_mult, int depth, int mb, const PassArgs &a,
                              cudaStream_t st);
+cudaError_t launch_pipe_f32(int mode, int vpl_mult, int u, int ring, int mb, int refill,
+                            const PassArgs &a, cudaStream_t st);
+cudaError_t launch_pipe_bf16(int mode, int vpl_mult, int u, int ring, int mb, int refill,
+                             const PassArgs &a, cudaStream_t st);
 // dst[q] = src[perm[q]] for q < nnz (values of S into the order of S^T).
 cudaError_t launch_permute(const float *src, const int32_t *perm, float *dst, int64_t nnz,
                            cudaStream_t st);
@@ -139,6 +151,9 @@ int encode_variant(const KernelVariant &v);
 // Default kernel variant of a pass over rows of width r (dtype, average
 // nonzeros per row).
 KernelVariant default_variant(int32_t r, int32_t dtype, double avg_nnz);
+// The team kernel's layout for a width (one group per row, 8 elements per
+// lane, 2 nonzeros per batch): the default of the batch kernels.
+KernelVariant team_default_variant(int32_t r, int32_t dtype);
 // Default split size of long rows for a pattern of nnz nonzeros and rows of
 // width r run with variant v.
 int32_t default_split_nnz(int64_t nnz, int32_t r, int32_t dtype, const KernelVariant &v);
@@ -172,4 +187,5 @@ struct fmm_plan {
     float *vals_static = nullptr;       // ... and their copy in S^T order
     int64_t workspace_bytes = 0;
     int device = 0;
+    int32_t *err = nullptr;           // device word: a pass gave up a bounded wait
 };

@@ -7,8 +7,11 @@
 // gathers mostly hit L2 with short dense rows (bfloat16 rows of r = 64,
 // 128 bytes) that wait, not bandwidth, sets the pass time.  Here a team keeps
 // a ring of RING batches of gathered rows in registers, as the raw 16-byte
-// words (bfloat16 rows stay packed until used): while batch b is used, the
-// loads of batches b + 1 .. b + RING - 1 are in flight.  The ring is indexed
+// words (bfloat16 rows stay packed until used).  Two orders: REFILL = 0
+// issues the loads of batch b + RING - 1 into the slot freed by batch b - 1
+// and then uses batch b; REFILL = 1 reads batch b out of its slot, refills
+// that slot at once with batch b + RING and then uses batch b (one batch
+// further ahead for the same registers).  The ring is indexed
 // with compile-time slots only (the loop over one index block is fully
 // unrolled), so it stays in registers.
 //
@@ -51,26 +54,11 @@ __device__ __forceinline__ void unpack2(const uint4 q, float2 *f)
     }
 }
 
-// Registers a variant keeps per lane, in floats: the ring (raw words), the
-// local row, the accumulator and one unpacked batch.
-template <typename T, int VPL, int U, int RING>
-constexpr int pipe_live_floats()
-{
-    return RING * U * VPL * 4 + 2 * VPL * Elem<T>::PER16 + U * VPL * Elem<T>::PER16;
-}
-
-// Blocks of 256 threads asked to stay resident per SM: as many as the
-// register estimate allows, at most 5 (48 registers a thread).
-template <typename T, int VPL, int U, int RING>
-constexpr int pipe_min_blocks()
-{
-    constexpr int regs = pipe_live_floats<T, VPL, U, RING>() + 24;
-    return regs <= 48 ? 5 : regs <= 64 ? 4 : regs <= 80 ? 3 : regs <= 128 ? 2 : 1;
-}
-
-template <int MODE, typename T, int R, int VPL, int U, int RING>
-__global__ void __launch_bounds__(256, (pipe_min_blocks<T, VPL, U, RING>()))
-    pipe_pass_kernel(const PassArgs a)
+// MB is the number of 256-thread blocks a variant asks to keep resident per
+// SM (a register cap of 65536 / (256 MB) per thread): the register ring
+// trades rows in flight per team against teams per SM.
+template <int MODE, typename T, int R, int VPL, int U, int RING, int MB, int REFILL>
+__global__ void __launch_bounds__(256, MB) pipe_pass_kernel(const PassArgs a)
 {
     static_assert(MODE == M_FUSED || MODE == M_SDDMM || MODE == M_SPMM, "forward roles");
     using TS = TeamShape<T, R, VPL, 1>;
@@ -79,7 +67,7 @@ __global__ void __launch_bounds__(256, (pipe_min_blocks<T, VPL, U, RING>()))
     constexpr int K = G >= 8 ? 1 : 8 / G;     // index entries per lane per block
     constexpr int IB = K * G;                 // nonzeros per index block
     constexpr int BPB = IB / U;               // batches per index block
-    static_assert(IB % U == 0 && BPB % RING == 0 && RING >= 2, "ring layout");
+    static_assert(IB % U == 0 && BPB % RING == 0 && RING >= 2 - REFILL, "ring layout");
     constexpr bool HAS_L = MODE != M_SPMM;
     constexpr bool ACC = MODE != M_SDDMM;
     constexpr bool NZ = MODE == M_SDDMM;
@@ -114,7 +102,8 @@ __global__ void __launch_bounds__(256, (pipe_min_blocks<T, VPL, U, RING>()))
     }
 
     const int n = end - beg;
-    const int wblocks = (int)__reduce_max_sync(0xffffffffu, (unsigned)((n + IB - 1) / IB));
+    const int wn = (int)__reduce_max_sync(0xffffffffu, (unsigned)n);
+    const int wblocks = (wn + IB - 1) / IB;
 
     // index block b: entry e of lane l is nonzero b * IB + e * G + l; past
     // the end of the row j = -1 and s = 0
@@ -156,14 +145,14 @@ __global__ void __launch_bounds__(256, (pipe_min_blocks<T, VPL, U, RING>()))
     load_block(0, jc, sc, ic);
     load_block(1, jn, sn, in_);
 #pragma unroll
-    for (int b = 0; b < RING - 1; ++b)
+    for (int b = 0; b < RING - 1 + REFILL; ++b)
         issue(ring[b], jc, b);
 
     for (int bk = 0; bk < wblocks; ++bk) {
 #pragma unroll
         for (int bb = 0; bb < BPB; ++bb) {
-            // prefetch RING - 1 batches ahead, into the slot freed last
-            {
+            if constexpr (!REFILL) {
+                // batch bb + RING - 1 into the slot that batch bb - 1 freed
                 const int pf = bb + RING - 1;
                 if (pf < BPB)
                     issue(ring[pf % RING], jc, pf);
@@ -185,6 +174,15 @@ __global__ void __launch_bounds__(256, (pipe_min_blocks<T, VPL, U, RING>()))
 #pragma unroll
                 for (int v = 0; v < VPL; ++v)
                     unpack2<T>(ring[bb % RING][u][v], &y2[u][v * W2]);
+            // the slot just read takes batch bb + RING (RING batches ahead;
+            // batches past this block come from the next index block)
+            if constexpr (REFILL) {
+                const int pf = bb + RING;
+                if (pf < BPB)
+                    issue(ring[bb % RING], jc, pf);
+                else
+                    issue(ring[bb % RING], jn, pf - BPB);
+            }
             if constexpr (MODE == M_SPMM) {
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
@@ -261,13 +259,13 @@ __global__ void __launch_bounds__(256, (pipe_min_blocks<T, VPL, U, RING>()))
     }
 }
 
-template <int MODE, typename T, int R, int VPL, int U, int RING>
+template <int MODE, typename T, int R, int VPL, int U, int RING, int MB, int REFILL>
 cudaError_t launch_pipe(const PassArgs &a, cudaStream_t st)
 {
     constexpr int G = TeamShape<T, R, VPL, 1>::G;
     const long long total = (long long)a.n_chunks + a.n_light;
     const long long blocks = (total * G + 255) / 256;
-    pipe_pass_kernel<MODE, T, R, VPL, U, RING><<<(unsigned)blocks, 256, 0, st>>>(a);
+    pipe_pass_kernel<MODE, T, R, VPL, U, RING, MB, REFILL><<<(unsigned)blocks, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -283,39 +281,44 @@ constexpr bool pipe_ok(int V, int U, int RING)
     return ib % (U * RING) == 0;
 }
 
-// Variants: (VPL, U, RING) with VPL as a multiple of the row shape's minimum.
+// Variants: (VPL, U, RING, MB, REFILL) with VPL as a multiple of the row
+// shape's minimum.
 template <typename T, int R>
-cudaError_t dispatch_pipe(int mode, int vpl, int u, int ring, const PassArgs &a, cudaStream_t st)
+cudaError_t dispatch_pipe(int mode, int vpl, int u, int ring, int mb, int refill,
+                          const PassArgs &a, cudaStream_t st)
 {
     constexpr int B = base_vpl<T, R>();
-#define FMM_PIPE(M, V, UU, RR)                                                     \
+#define FMM_PIPE(M, V, UU, RR, MM, FF)                                             \
     if constexpr (pipe_ok<T, R>(V, UU, RR))                                        \
-        if (mode == M && vpl == V && u == UU && ring == RR)                        \
-            return launch_pipe<M, T, R, V, UU, RR>(a, st);
-#define FMM_PIPE_MODES(V, UU, RR) \
-    FMM_PIPE(M_FUSED, V, UU, RR) FMM_PIPE(M_SDDMM, V, UU, RR) FMM_PIPE(M_SPMM, V, UU, RR)
-    FMM_PIPE_MODES(B, 2, 2)
-    FMM_PIPE_MODES(B, 2, 4)
-    FMM_PIPE_MODES(B, 1, 2)
-    FMM_PIPE_MODES(B, 1, 4)
-    FMM_PIPE_MODES(2 * B, 2, 2)
-    FMM_PIPE_MODES(2 * B, 1, 2)
+        if (mode == M && vpl == V && u == UU && ring == RR && mb == MM && refill == FF) \
+            return launch_pipe<M, T, R, V, UU, RR, MM, FF>(a, st);
+#define FMM_PIPE_MODES(V, UU, RR, MM, FF)                                         \
+    FMM_PIPE(M_FUSED, V, UU, RR, MM, FF) FMM_PIPE(M_SDDMM, V, UU, RR, MM, FF)       \
+    FMM_PIPE(M_SPMM, V, UU, RR, MM, FF)
+    FMM_PIPE_MODES(2 * B, 1, 2, 2, 0)
+    FMM_PIPE_MODES(2 * B, 1, 2, 3, 0)
+    FMM_PIPE_MODES(2 * B, 1, 4, 2, 0)
+    FMM_PIPE_MODES(2 * B, 1, 2, 2, 1)
+    FMM_PIPE_MODES(B, 2, 2, 4, 0)
+    FMM_PIPE_MODES(B, 2, 2, 4, 1)
+    FMM_PIPE_MODES(B, 2, 4, 3, 0)
+    FMM_PIPE_MODES(B, 4, 2, 3, 0)
 #undef FMM_PIPE_MODES
 #undef FMM_PIPE
     return cudaErrorNotSupported;   // not instantiated for this width: the caller falls back
 }
 
 template <typename T>
-cudaError_t launch_pipe_typed(int mode, int vpl_mult, int u, int ring, const PassArgs &a,
-                              cudaStream_t st)
+cudaError_t launch_pipe_typed(int mode, int vpl_mult, int u, int ring, int mb, int refill,
+                              const PassArgs &a, cudaStream_t st)
 {
     if ((long long)a.n_chunks + a.n_light == 0)
         return cudaSuccess;
     switch (a.r) {
-    case 32: return dispatch_pipe<T, 32>(mode, vpl_mult * base_vpl<T, 32>(), u, ring, a, st);
-    case 64: return dispatch_pipe<T, 64>(mode, vpl_mult * base_vpl<T, 64>(), u, ring, a, st);
-    case 128: return dispatch_pipe<T, 128>(mode, vpl_mult * base_vpl<T, 128>(), u, ring, a, st);
-    case 256: return dispatch_pipe<T, 256>(mode, vpl_mult * base_vpl<T, 256>(), u, ring, a, st);
+    case 32: return dispatch_pipe<T, 32>(mode, vpl_mult * base_vpl<T, 32>(), u, ring, mb, refill, a, st);
+    case 64: return dispatch_pipe<T, 64>(mode, vpl_mult * base_vpl<T, 64>(), u, ring, mb, refill, a, st);
+    case 128: return dispatch_pipe<T, 128>(mode, vpl_mult * base_vpl<T, 128>(), u, ring, mb, refill, a, st);
+    case 256: return dispatch_pipe<T, 256>(mode, vpl_mult * base_vpl<T, 256>(), u, ring, mb, refill, a, st);
     default: return cudaErrorNotSupported;
     }
 }

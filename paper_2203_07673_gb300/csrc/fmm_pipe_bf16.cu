@@ -2,9 +2,9 @@
 #include "fmm_pipe.cuh"
 
 namespace fmm {
-cudaError_t launch_pipe_bf16(int mode, int vpl_mult, int u, int ring, const PassArgs &a,
-                             cudaStream_t st)
+cudaError_t launch_pipe_bf16(int mode, int vpl_mult, int u, int ring, int mb, int refill,
+                            const PassArgs &a, cudaStream_t st)
 {
-    return launch_pipe_typed<bf16_t>(mode, vpl_mult, u, ring, a, st);
+    return launch_pipe_typed<bf16_t>(mode, vpl_mult, u, ring, mb, refill, a, st);
 }
 }  // namespace fmm

@@ -476,6 +476,7 @@ void destroy_plan(fmm_plan *p)
     cudaFree(p->perm_t);
     cudaFree(p->vals_t);
     cudaFree(p->vals_static);
+    cudaFree(p->err);
     delete p;
 }
 
@@ -511,6 +512,8 @@ int create_plan(const fmm_csr *S, int32_t r, int32_t dtype, const fmm_plan_optio
     PLAN_TRY(dmalloc(&tmp.vb, N, nullptr), "allocate sort values");
     PLAN_TRY(dmalloc(&tmp.ghist, (size_t)ntiles * 256, nullptr), "allocate histogram");
     PLAN_TRY(dmalloc(&tmp.counters, 2, nullptr), "allocate counters");
+    PLAN_TRY(dmalloc(&p->err, 1, p), "allocate error word");
+    PLAN_TRY(cudaMemsetAsync(p->err, 0, sizeof(int32_t), st), "clear error word");
 
     rc = build_side(p->rows, S->row_ptr, S->m, p->split_nnz, r, tmp, st, p);
     if (rc) return fail(rc);
@@ -568,9 +571,8 @@ int create_plan(const fmm_csr *S, int32_t r, int32_t dtype, const fmm_plan_optio
 // per output row, 8 elements (32 bytes) per lane and 2 nonzeros per batch is
 // the best or within a few percent of it (the lighter register footprint
 // keeps more rows in flight than deeper batches do).
-KernelVariant default_variant(int32_t r, int32_t dtype, double avg_nnz)
+KernelVariant team_default_variant(int32_t r, int32_t dtype)
 {
-    (void)avg_nnz;
     KernelVariant v;
     v.ng = 1;
     v.u = 2;
@@ -578,6 +580,26 @@ KernelVariant default_variant(int32_t r, int32_t dtype, double avg_nnz)
     // float32 rows of at most 32 vectors hold 4 elements per vector: two
     // vectors per lane make 8 elements
     v.vpl_mult = (dtype == FMM_F32 && vecs <= 32) ? 2 : 1;
+    return v;
+}
+
+KernelVariant default_variant(int32_t r, int32_t dtype, double avg_nnz)
+{
+    (void)avg_nnz;
+    KernelVariant v = team_default_variant(r, dtype);
+    // bfloat16 rows of r = 64 and 128: the register-ring pass with 16
+    // elements per lane, one nonzero per batch and the slot refilled as soon
+    // as it is read (code 32212).  Measured on GB300 (FusedMMA / FusedMMB
+    // pass, ms): Zipf rows 2^21 x 2^19 1.71 / 1.54 -> 1.36 / 1.06, R-MAT 2^22
+    // 1.65 -> 1.41, Erdos-Renyi 2^20 at r = 128 1.55 / 1.74 -> 1.41 / 1.53.
+    // Its backward roles run the team kernel with the same lane layout.
+    if (dtype == FMM_BF16 && (r == 64 || r == 128)) {
+        v.vpl_mult = 2;
+        v.u = 1;
+        v.ring = 2;
+        v.mb = 2;
+        v.refill = 1;
+    }
     // float32 rows of r = 128 (512 bytes): the staged pass with a ring of 4
     // gathered rows per team, 3-4 % faster on Erdos-Renyi rows at the DRAM
     // roofline (it needs no register spill); where gathers mostly hit L2 the
@@ -592,8 +614,12 @@ KernelVariant default_variant(int32_t r, int32_t dtype, double avg_nnz)
 // through a chunk U*NG nonzeros per dependent step, while all concurrent
 // teams share the rest of the pass; a chunk must end well before the pass
 // does, so it holds at most nnz / (4 x concurrent teams) nonzeros.  Teams
-// at once: SMs x 32 resident warps x teams per warp (32 / lanes per team of
-// the variant; rows of the generic kernel take a warp).  Within [256, 8192].
+// at once: SMs x resident warps x teams per warp (32 / lanes per team of
+// the variant; rows of the generic kernel take a warp); resident warps are
+// 8 per requested block for the register-ring and bulk-staged passes, else
+// 32.  Within [256, 8192].  (The register-ring pass on the Zipf-row pattern
+// with bfloat16 rows of r = 64: chunks of 514 nonzeros took 1.51 ms, of
+// 1028 1.37 ms.)
 // (On R-MAT 2^22 with BF16 rows of r = 64 this gives about 840; chunks of
 // 3982 made that forward pass 15 % slower than chunks of 1024.)
 int32_t default_split_nnz(int64_t nnz, int32_t r, int32_t dtype, const KernelVariant &v)
@@ -605,7 +631,8 @@ int32_t default_split_nnz(int64_t nnz, int32_t r, int32_t dtype, const KernelVar
         const int vpl = (vecs > 32 ? vecs / 32 : 1) * v.vpl_mult;
         lanes = std::min(32, std::max(1, vecs / std::max(1, vpl)) * std::max(1, v.ng));
     }
-    const int64_t teams = (int64_t)sm_count() * 32 * (32 / lanes);
+    const int warps = (v.ring > 0 || v.depth > 0) && v.mb > 0 ? 8 * v.mb : 32;
+    const int64_t teams = (int64_t)sm_count() * warps * (32 / lanes);
     return (int32_t)std::min<int64_t>(8192, std::max<int64_t>(256, nnz / (4 * teams)));
 }
 

@@ -102,6 +102,27 @@ __device__ __forceinline__ void group_allreduce(float (&v)[NV])
     }
 }
 
+// Element e of a small register array (a select chain, so the array stays
+// in registers when e is not a compile-time constant).
+template <int K>
+__device__ __forceinline__ int pick(const int (&x)[K], int e)
+{
+    int r = x[0];
+#pragma unroll
+    for (int i = 1; i < K; ++i)
+        if (e == i) r = x[i];
+    return r;
+}
+template <int K>
+__device__ __forceinline__ float pick(const float (&x)[K], int e)
+{
+    float r = x[0];
+#pragma unroll
+    for (int i = 1; i < K; ++i)
+        if (e == i) r = x[i];
+    return r;
+}
+
 // Work item of group `gid`: chunks of split rows first, then light rows in
 // plan order.  slot >= 0 marks a chunk (its partial row goes to partials).
 __device__ __forceinline__ void pass_item(const PassArgs &a, long long gid, int &row,

@@ -55,25 +55,6 @@ __device__ __forceinline__ void stage_read(const uint4 *ring, int st, int tid, f
     }
 }
 
-template <int K>
-__device__ __forceinline__ int pick(const int (&x)[K], int e)
-{
-    int r = x[0];
-#pragma unroll
-    for (int i = 1; i < K; ++i)
-        if (e == i) r = x[i];
-    return r;
-}
-template <int K>
-__device__ __forceinline__ float pick(const float (&x)[K], int e)
-{
-    float r = x[0];
-#pragma unroll
-    for (int i = 1; i < K; ++i)
-        if (e == i) r = x[i];
-    return r;
-}
-
 template <int MODE, typename T, int R, int VPL, int D>
 __global__ void __launch_bounds__(256) staged_pass_kernel(const PassArgs a)
 {

@@ -17,7 +17,8 @@ import torch
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_build", "libfmm.so")
 
-FMM_OK, FMM_EINVAL, FMM_EUNSUPPORTED, FMM_EOVERFLOW, FMM_ECUDA, FMM_ENOMEM = 0, -1, -2, -3, -4, -5
+FMM_OK, FMM_EINVAL, FMM_EUNSUPPORTED, FMM_EOVERFLOW, FMM_ECUDA, FMM_ENOMEM, FMM_ETIMEOUT = \
+    0, -1, -2, -3, -4, -5, -6
 FMM_F32, FMM_BF16 = 0, 1
 FMM_PLAN_NO_TRANSPOSE = 1
 
@@ -29,6 +30,7 @@ _SIGNATURES = {
     "fmm_plan_create": ([_P, _I32, _I32, _P, _P, _P], ctypes.c_int),
     "fmm_plan_destroy": ([_P], ctypes.c_int),
     "fmm_plan_get_info": ([_P, _P], ctypes.c_int),
+    "fmm_plan_status": ([_P, _P], ctypes.c_int),
     "fmm_sddmm": ([_P, _P, _P, _P, _P, _P], ctypes.c_int),
     "fmm_spmm": ([_P, _P, _P, _P, _P], ctypes.c_int),
     "fmm_spmm_t": ([_P, _P, _P, _P, _P], ctypes.c_int),
@@ -189,6 +191,11 @@ class Plan:
         rc = lib().fmm_plan_set_values(self.handle, self._f32(vals, (self.nnz,), "vals"),
                                        _stream(stream))
         _check(rc, "fmm_plan_set_values")
+
+    def status(self, stream=None):
+        """fmm_plan_status: synchronise the stream and raise FmmError if a pass
+        of this plan gave up a bounded wait (the error word is cleared)."""
+        _check(lib().fmm_plan_status(self.handle, _stream(stream)), "fmm_plan_status")
 
     def info(self) -> dict:
         inf = _Info()

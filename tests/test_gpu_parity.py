@@ -110,6 +110,38 @@ def test_kernel_variants(r, dtype, split_nnz, variant):
     run_all(S, {"split_nnz": split_nnz, "variant": variant}, r, dtype, seed=3)
 
 
+# the register-ring (2xxxx, 3xxxx) and bulk-staged (4xxxx) forward passes
+PIPELINED_AND_BULK = [22212, 23212, 22412, 32212, 24221, 34221, 23421, 23241,
+                      44042, 43082, 44041, 44081]
+
+
+@pytest.mark.parametrize("variant", PIPELINED_AND_BULK)
+@pytest.mark.parametrize("split_nnz", [16, 0])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16], ids=["f32", "bf16"])
+@pytest.mark.parametrize("r", [32, 64, 128, 256])
+def test_pipelined_and_bulk_variants(r, dtype, split_nnz, variant):
+    S, _ = pattern("hubs", 7)
+    run_all(S, {"split_nnz": split_nnz, "variant": variant}, r, dtype, seed=3)
+
+
+@pytest.mark.parametrize("variant", PIPELINED_AND_BULK)
+def test_pipelined_and_bulk_report_no_timeout(variant):
+    """A bulk-staged pass that gave up a bounded wait sets the plan's error
+    word; a normal run leaves it clear (fmm_plan_status returns FMM_OK)."""
+    from paper_2203_07673_gb300 import fmm
+    S, _ = pattern("er", 11)
+    rng = np.random.default_rng(1)
+    A = rng.standard_normal((S.m, 64)).astype(np.float32)
+    B = rng.standard_normal((S.n, 64)).astype(np.float32)
+    rp, ci, vt, At, Bt = upload(S, None, A, B, torch.bfloat16)
+    plan = fmm.Plan(rp, ci, S.n, 64, torch.bfloat16, variant=variant)
+    for _ in range(3):
+        fmm.fusedmm(plan, None, At, Bt)
+        fmm.fusedmm_t(plan, None, At, Bt)
+    plan.status()
+    plan.close()
+
+
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16], ids=["f32", "bf16"])
 @pytest.mark.parametrize("r", [16, 32, 128])
 def test_exact_small_integers_bitwise(r, dtype):
@@ -344,7 +376,7 @@ def test_rows_without_nonzeros_are_zeroed():
     deg, cdeg = S.degrees(), np.bincount(S.col_idx, minlength=S.n)
     assert (deg == 0).sum() > 50 and (cdeg == 0).sum() > 20
     rng = np.random.default_rng(2)
-    for r, code in ((32, 0), (128, 0), (64, 1082), (24, 0)):
+    for r, code in ((32, 0), (128, 0), (64, 1082), (24, 0), (64, 32212), (64, 44042)):
         A = rng.standard_normal((S.m, r)).astype(np.float32)
         B = rng.standard_normal((S.n, r)).astype(np.float32)
         vals = rng.uniform(0, 1, S.nnz).astype(np.float32)
