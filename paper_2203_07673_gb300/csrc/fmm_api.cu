@@ -207,7 +207,7 @@ int run_pass(const fmm_plan *p, const Side &side, int mode, const float *s, cons
         } else {
             // values of S gathered once into the order of S^T, so the pass
             // streams them instead of fetching one scattered word per nonzero
-            e = launch_permute(s, side.perm, p->vals_t, p->nnz, st);
+            e = launch_values_t(p, s, p->vals_t, st);
             a.s = p->vals_t;
         }
         a.s_direct = 1;
@@ -288,7 +288,7 @@ int fmm_plan_set_values(fmm_plan *p, const float *vals, fmm_stream stream)
         }
         p->workspace_bytes += (int64_t)sizeof(float) * p->nnz;
     }
-    cudaError_t e = launch_permute(vals, p->perm_t, p->vals_static, p->nnz, (cudaStream_t)stream);
+    cudaError_t e = launch_values_t(p, vals, p->vals_static, (cudaStream_t)stream);
     if (e != cudaSuccess) {
         set_error("fmm_plan_set_values", e);
         return FMM_ECUDA;

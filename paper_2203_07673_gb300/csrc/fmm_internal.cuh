@@ -137,6 +137,12 @@ cudaError_t launch_pipe_bf16(int mode, int vpl_mult, int u, int ring, int mb, in
 // dst[q] = src[perm[q]] for q < nnz (values of S into the order of S^T).
 cudaError_t launch_permute(const float *src, const int32_t *perm, float *dst, int64_t nnz,
                            cudaStream_t st);
+// Values of S in the order of S^T for a plan: the windowed two-pass
+// permutation where the plan has it, else launch_permute.
+cudaError_t launch_values_t(const fmm_plan *p, const float *src, float *dst, cudaStream_t st);
+// S^T slots per window of the windowed permutation (32 MB of float32 values:
+// a window's staging values stay in L2 while its slots are filled).
+constexpr int64_t kPermuteWindow = int64_t(1) << 23;
 // Sums the partial rows of every split row, in chunk order, into out.
 cudaError_t launch_combine(const Side &side, float *out, int32_t r,
                            cudaStream_t st);
@@ -188,4 +194,10 @@ struct fmm_plan {
     int64_t workspace_bytes = 0;
     int device = 0;
     int32_t *err = nullptr;           // device word: a pass gave up a bounded wait
+    // windowed value permutation (plans with more than 2 windows of
+    // nonzeros): S-order slot p -> its place in the window staging array,
+    // S^T slot q -> where its value waits there, and the staging array
+    int32_t *win_pos1 = nullptr;
+    int32_t *win_pos2 = nullptr;
+    float *win_tmp = nullptr;
 };

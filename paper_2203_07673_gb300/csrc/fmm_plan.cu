@@ -272,6 +272,36 @@ __global__ void rows_of_kernel(const int32_t *row_ptr, int32_t m, const int32_t 
     }
 }
 
+// Windowed value permutation, plan time.  Window w holds the S^T slots
+// [w P, (w + 1) P).  key[perm[q]] = q / P (the window of each S slot's
+// destination), val[p] = p; a stable sort by key lists, per window, its
+// source slots in S order, so sorted position i of slot p is pos1[p]; then
+// pos2[q] = pos1[perm[q]] is where the value of S^T slot q waits in pass 2.
+__global__ void window_keys_kernel(const int32_t *perm, int64_t nnz, int64_t P, uint32_t *keys,
+                                   int32_t *vals)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nnz; q += stride) {
+        keys[perm[q]] = (uint32_t)(q / P);
+        vals[q] = (int32_t)q;
+    }
+}
+
+__global__ void window_pos1_kernel(const int32_t *sorted_slots, int64_t nnz, int32_t *pos1)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += stride)
+        pos1[sorted_slots[i]] = (int32_t)i;
+}
+
+__global__ void window_pos2_kernel(const int32_t *perm, const int32_t *pos1, int64_t nnz,
+                                   int32_t *pos2)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nnz; q += stride)
+        pos2[q] = pos1[perm[q]];
+}
+
 }  // namespace fmm
 
 // ====================================================================== API
@@ -476,6 +506,9 @@ void destroy_plan(fmm_plan *p)
     cudaFree(p->perm_t);
     cudaFree(p->vals_t);
     cudaFree(p->vals_static);
+    cudaFree(p->win_pos1);
+    cudaFree(p->win_pos2);
+    cudaFree(p->win_tmp);
     cudaFree(p->err);
     delete p;
 }
@@ -551,6 +584,27 @@ int create_plan(const fmm_csr *S, int32_t r, int32_t dtype, const fmm_plan_optio
             PLAN_TRY(cudaGetLastError(), "transpose rows");
         }
         PLAN_TRY(dmalloc(&p->vals_t, (size_t)S->nnz, p), "allocate S^T values");
+        if (S->nnz > 2 * kPermuteWindow) {
+            // the windowed value permutation (launch_values_t)
+            const int64_t P = kPermuteWindow;
+            const int64_t W = (S->nnz + P - 1) / P;
+            int wbits = 0;
+            while ((int64_t(1) << wbits) < W) ++wbits;
+            PLAN_TRY(dmalloc(&p->win_pos1, (size_t)S->nnz, p), "allocate window positions");
+            PLAN_TRY(dmalloc(&p->win_pos2, (size_t)S->nnz, p), "allocate window positions");
+            PLAN_TRY(dmalloc(&p->win_tmp, (size_t)S->nnz, p), "allocate window values");
+            window_keys_kernel<<<blocks_for(S->nnz, 256, sm_count() * 32), 256, 0, st>>>(
+                p->perm_t, S->nnz, P, tmp.ka, tmp.va);
+            PLAN_TRY(cudaGetLastError(), "window keys");
+            bool wb = false;
+            PLAN_TRY(radix_sort(tmp.ka, tmp.va, tmp.kb, tmp.vb, S->nnz, wbits, tmp.ghist, st, &wb),
+                     "window sort");
+            window_pos1_kernel<<<blocks_for(S->nnz, 256, sm_count() * 32), 256, 0, st>>>(
+                wb ? tmp.vb : tmp.va, S->nnz, p->win_pos1);
+            window_pos2_kernel<<<blocks_for(S->nnz, 256, sm_count() * 32), 256, 0, st>>>(
+                p->perm_t, p->win_pos1, S->nnz, p->win_pos2);
+            PLAN_TRY(cudaGetLastError(), "window positions");
+        }
         rc = build_side(p->cols, p->row_ptr_t, S->n, p->split_nnz, r, tmp, st, p);
         if (rc) return fail(rc);
         p->cols.col_idx = p->col_idx_t;
@@ -678,6 +732,38 @@ cudaError_t launch_permute(const float *src, const int32_t *perm, float *dst, in
     const int64_t per_block = kPermuteBlock * kPermutePerThread;
     const int64_t blocks = (nnz + per_block - 1) / per_block;   // nnz < 2^31: < 2^21 blocks
     permute_kernel<<<(unsigned)blocks, kPermuteBlock, 0, st>>>(src, perm, dst, nnz);
+    return cudaGetLastError();
+}
+
+// dst[pos[p]] = src[p]: the first pass of the windowed permutation.  Reads
+// are coalesced; the values of a block go to a few runs (one per window), so
+// the stores stay mostly whole sectors.
+__global__ void __launch_bounds__(kPermuteBlock) scatter_kernel(const float *src,
+                                                               const int32_t *pos, float *dst,
+                                                               int64_t nnz)
+{
+    const int64_t base =
+        (int64_t)blockIdx.x * (kPermuteBlock * kPermutePerThread) + threadIdx.x;
+#pragma unroll
+    for (int j = 0; j < kPermutePerThread; ++j) {
+        const int64_t p = base + (int64_t)kPermuteBlock * j;
+        if (p < nnz)
+            dst[__ldcs(pos + p)] = __ldcs(src + p);
+    }
+}
+
+cudaError_t launch_values_t(const fmm_plan *p, const float *src, float *dst, cudaStream_t st)
+{
+    if (p->nnz == 0 || !src)
+        return cudaSuccess;
+    if (!p->win_pos1)
+        return launch_permute(src, p->perm_t, dst, p->nnz, st);
+    const int64_t per_block = kPermuteBlock * kPermutePerThread;
+    const int64_t blocks = (p->nnz + per_block - 1) / per_block;
+    scatter_kernel<<<(unsigned)blocks, kPermuteBlock, 0, st>>>(src, p->win_pos1, p->win_tmp,
+                                                              p->nnz);
+    permute_kernel<<<(unsigned)blocks, kPermuteBlock, 0, st>>>(p->win_tmp, p->win_pos2, dst,
+                                                              p->nnz);
     return cudaGetLastError();
 }
 

@@ -223,3 +223,34 @@ def test_batched_512_matrices_sampled():
     batch.close()
     for it in items:
         it["plan"].close()
+
+
+def test_windowed_value_permutation_exact():
+    """Plans with more than two windows (2^23 S^T slots each) of nonzeros put
+    the values of S into S^T order in two passes (scatter into windows, then
+    gather inside a window).  With small-integer values and all-ones A and
+    B, FusedMMB and SpMMB are exact integer column sums of S, so every
+    element must equal the column sums bit for bit; per-call and registered
+    values both take the windowed path."""
+    from paper_2203_07673_gb300 import fmm
+    dev = torch.device("cuda")
+    g = wl._torch_gen(dev, 4242)
+    m, n, deg, r = 600_000, 1 << 18, 30, 32
+    rp, ci = wl.er_exact_degree_torch(m, n, deg, g, dev)
+    nnz = ci.numel()
+    assert nnz > 2 * (1 << 23)
+    vals = (torch.arange(nnz, device=dev) % 7).float()
+    A = torch.ones(m, r, device=dev)
+    B = torch.ones(n, r, device=dev)
+    plan = fmm.Plan(rp, ci, n, r)
+    colsum = torch.bincount(ci.long(), weights=vals.double(), minlength=n)
+    want_t = (colsum * r).float()[:, None].expand(n, r)
+    assert torch.equal(fmm.fusedmm_t(plan, vals, A, B), want_t)
+    assert torch.equal(fmm.spmm_t(plan, vals, A), colsum.float()[:, None].expand(n, r))
+    plan.set_values(vals)
+    assert torch.equal(fmm.fusedmm_t(plan, vals, A, B), want_t)
+    # values changed after registration are taken from the new pointer
+    vals2 = (torch.arange(nnz, device=dev) % 5).float()
+    colsum2 = torch.bincount(ci.long(), weights=vals2.double(), minlength=n)
+    assert torch.equal(fmm.fusedmm_t(plan, vals2, A, B), (colsum2 * r).float()[:, None].expand(n, r))
+    plan.close()
