@@ -115,9 +115,10 @@ def _calls(k, m, n, nnz, r, e, vals_given, model):
     if k == 3:
         # backward: pass over S (A_i, G_i local, B_j gathered, dA and ds written),
         # pass over S^T (B_j local, A_i and G_i gathered, dB written)
-        p1 = model(m, n, nnz, r, e, True) + 4 * m * r + 4 * nnz
+        p1 = model(m, n, nnz, r, e, vals_given) + 4 * m * r + 4 * nnz
         g_rows = nnz if model is gather_model_bytes_mn else m   # G_i with each gathered A_i
-        p2 = model(n, m, nnz, r, e, True) + 4 * g_rows * r + permute_bytes(nnz)
+        p2 = model(n, m, nnz, r, e, vals_given) + 4 * g_rows * r + (
+            permute_bytes(nnz) if vals_given else 0)
         return [("fmm_fusedmm", fwd), ("fmm_fusedmm_bwd", p1 + p2)]
     return [("fmm_fusedmm", fwd), ("fmm_fusedmm_t", fwd_t)]
 
@@ -474,8 +475,9 @@ def run_fmm(args, rank, world, local_rank):
     rp = torch.from_numpy(S.row_ptr).to(dev)
     ci = torch.from_numpy(S.col_idx).to(dev)
     if k == 3:
-        # s = 1 with a gradient wanted: the values are an explicit ones vector
-        vals = torch.ones(S.nnz, device=dev)
+        # s = 1: vals = NULL, the library's every-value-is-one, which still
+        # gives the gradient with respect to the values (ds)
+        vals = None
     else:
         vals = None if w["vals"] is None else torch.from_numpy(w["vals"]).to(dev)
     A = torch.from_numpy(w["A"]).to(dev).to(tdt).contiguous()
@@ -500,8 +502,9 @@ def run_fmm(args, rank, world, local_rank):
 
     def call_second():
         if k == 3:
-            rc = lib.fmm_fusedmm_bwd(plan.handle, vals.data_ptr(), A.data_ptr(), B.data_ptr(),
-                                     G.data_ptr(), dA.data_ptr(), dB.data_ptr(), ds.data_ptr(), sp)
+            rc = lib.fmm_fusedmm_bwd(plan.handle, None if vals is None else vals.data_ptr(),
+                                     A.data_ptr(), B.data_ptr(), G.data_ptr(), dA.data_ptr(),
+                                     dB.data_ptr(), ds.data_ptr(), sp)
             fmm._check(rc, "fmm_fusedmm_bwd")
         else:
             fmm.fusedmm_t(plan, vals, A, B, out=out_t)
@@ -596,7 +599,8 @@ def run_fmm(args, rank, world, local_rank):
         o = slot_out[slot]
         fmm.fusedmm(plan, vb, Ab, Bb, out=o[0])
         if k == 3:
-            rc = lib.fmm_fusedmm_bwd(plan.handle, vb.data_ptr(), Ab.data_ptr(), Bb.data_ptr(),
+            rc = lib.fmm_fusedmm_bwd(plan.handle, None if vb is None else vb.data_ptr(),
+                                     Ab.data_ptr(), Bb.data_ptr(),
                                      Gb.data_ptr(), o[2].data_ptr(), o[1].data_ptr(),
                                      o[3].data_ptr(), torch.cuda.current_stream().cuda_stream)
             fmm._check(rc, "fmm_fusedmm_bwd")
@@ -620,9 +624,13 @@ def run_fmm(args, rank, world, local_rank):
     dom_name, dom_bytes = calls[dom]
     achieved = dom_bytes / (call_ms[dom] / 1e3) / 1e9
     traffic, traffic_note = read_traffic(w["name"], dom_name, w["dtype"])
+    # the value permutation of a pass over S^T: one launch, or two (scatter
+    # into windows, gather inside them) above two windows of 2^23 slots
+    perm_launches = 0 if vals is None else (2 if S.nnz > 2 * (1 << 23) else 1)
     launches = {"fmm_fusedmm": 1 + (1 if info["split_rows"] else 0),
-                "fmm_fusedmm_t": 1 + (1 if info["split_cols"] else 0) + (1 if vals is not None else 0),
-                "fmm_fusedmm_bwd": 3 + (1 if info["split_rows"] else 0) + (1 if info["split_cols"] else 0)}
+                "fmm_fusedmm_t": 1 + (1 if info["split_cols"] else 0) + perm_launches,
+                "fmm_fusedmm_bwd": 2 + (1 if info["split_rows"] else 0)
+                + (1 if info["split_cols"] else 0) + perm_launches}
     h2d = A_h.numel() * A_h.element_size() + B_h.numel() * B_h.element_size() + (
         0 if vals_h is None else vals_h.numel() * 4) + (0 if G_h is None else G_h.numel() * 4)
     d2h = (out_h.numel() + second_h.numel()) * 4 + (

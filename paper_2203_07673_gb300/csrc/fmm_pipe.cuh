@@ -28,8 +28,13 @@
 // past the end of a row get value 0 and a zero row, so every batch runs the
 // same instructions and contributes exactly nothing.
 //
-// Roles: FusedMM, SDDMM, SpMM (the forward roles), one team of G lanes per
-// row or chunk of a split row.
+// Roles: FusedMM, SDDMM, SpMM (instantiated), and the two adjoint passes:
+// over S (two dot products of the gathered row, against the local row and
+// the local float32 gradient row; ds written) and over S^T (the gathered row
+// and its float32 gradient row both in the ring).  The adjoint roles are not
+// instantiated: on R-MAT 2^22 with bfloat16 rows of r = 64 they took 5.4-5.6
+// ms for the backward against 5.2 ms with the team kernel.  One team of G
+// lanes per row or chunk of a split row.
 #pragma once
 
 #include "fmm_rows.cuh"
@@ -60,7 +65,7 @@ __device__ __forceinline__ void unpack2(const uint4 q, float2 *f)
 template <int MODE, typename T, int R, int VPL, int U, int RING, int MB, int REFILL>
 __global__ void __launch_bounds__(256, MB) pipe_pass_kernel(const PassArgs a)
 {
-    static_assert(MODE == M_FUSED || MODE == M_SDDMM || MODE == M_SPMM, "forward roles");
+    static_assert(MODE >= M_FUSED && MODE <= M_BWD_COL, "role");
     using TS = TeamShape<T, R, VPL, 1>;
     constexpr int G = TS::G, E = TS::E, EPV = TS::EPV;
     constexpr int E2 = E / 2, W2 = EPV / 2;   // float pairs per lane; per 16-byte word
@@ -70,7 +75,12 @@ __global__ void __launch_bounds__(256, MB) pipe_pass_kernel(const PassArgs a)
     static_assert(IB % U == 0 && BPB % RING == 0 && RING >= 2 - REFILL, "ring layout");
     constexpr bool HAS_L = MODE != M_SPMM;
     constexpr bool ACC = MODE != M_SDDMM;
-    constexpr bool NZ = MODE == M_SDDMM;
+    constexpr bool NZ = MODE == M_SDDMM || MODE == M_BWD_ROW;
+    constexpr bool TWO = MODE == M_BWD_ROW || MODE == M_BWD_COL;   // two dot products
+    constexpr bool LOCAL_H = MODE == M_BWD_ROW;    // float32 gradient row, local
+    constexpr bool GATHER_H = MODE == M_BWD_COL;   // float32 gradient row, gathered
+    constexpr int HW = GATHER_H ? VPL * EPV / 4 : 1;   // float4 words of a gathered H row
+    constexpr int ND = TWO ? 2 * U : U;                // dot products per batch
 
     const int lane = threadIdx.x & 31;
     const int lig = lane & (G - 1);
@@ -86,12 +96,28 @@ __global__ void __launch_bounds__(256, MB) pipe_pass_kernel(const PassArgs a)
     const T *L = static_cast<const T *>(a.L);
     const T *Y = static_cast<const T *>(a.Y);
 
-    float2 l2[E2], acc2[E2];
+    float2 l2[E2], acc2[E2], h2[LOCAL_H ? E2 : 1];
 #pragma unroll
     for (int e = 0; e < E2; ++e) {
         l2[e] = make_float2(0.f, 0.f);
         acc2[e] = make_float2(0.f, 0.f);
     }
+    h2[0] = make_float2(0.f, 0.f);
+    // a float32 row in T's element mapping (word v of the lane holds EPV
+    // elements): EPV / 4 float4 per word
+    auto load_h = [&](const float *hrow, float2 *f, bool gather) {
+#pragma unroll
+        for (int v = 0; v < VPL; ++v)
+#pragma unroll
+            for (int q = 0; q < EPV / 4; ++q) {
+                const float4 x = ld.f4(hrow + (v * G + lig) * EPV + 4 * q, gather);
+                f[v * W2 + 2 * q] = make_float2(x.x, x.y);
+                f[v * W2 + 2 * q + 1] = make_float2(x.z, x.w);
+            }
+    };
+    if constexpr (LOCAL_H)
+        if (active && end > beg)
+            load_h(a.H + (size_t)row * R, h2, false);
     if (HAS_L && active && end > beg) {
 #pragma unroll
         for (int v = 0; v < VPL; ++v) {
@@ -109,6 +135,11 @@ __global__ void __launch_bounds__(256, MB) pipe_pass_kernel(const PassArgs a)
     // the end of the row j = -1 and s = 0
     int jc[K], jn[K], ic[K], in_[K];
     float sc[K], sn[K];
+    // per-nonzero outputs (SDDMM): the lane holding a nonzero's index entry
+    // keeps its value and stores the block's values at once
+    float held[K];
+#pragma unroll
+    for (int e = 0; e < K; ++e) held[e] = 0.f;
     auto load_block = [&](int b, int (&j)[K], float (&s)[K], int (&si)[K]) {
 #pragma unroll
         for (int e = 0; e < K; ++e) {
@@ -125,6 +156,7 @@ __global__ void __launch_bounds__(256, MB) pipe_pass_kernel(const PassArgs a)
     };
 
     uint4 ring[RING][U][VPL];
+    float4 hring[GATHER_H ? RING : 1][U][HW];
 
     // gathers of batch bb (block-local) of the block whose indices are j
     auto issue = [&](uint4 (&dst)[U][VPL], const int (&j)[K], int bb) {
@@ -141,12 +173,34 @@ __global__ void __launch_bounds__(256, MB) pipe_pass_kernel(const PassArgs a)
             }
         }
     };
+    // the gathered float32 gradient rows of the same batch
+    auto issue_h = [&](float4 (&dst)[U][HW], const int (&j)[K], int bb) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int t = bb * U + u;
+            const int jj = __shfl_sync(0xffffffffu, j[t / G], tbase + (t % G));
+#pragma unroll
+            for (int v = 0; v < VPL; ++v)
+#pragma unroll
+                for (int q = 0; q < EPV / 4; ++q) {
+                    dst[u][v * (EPV / 4) + q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (jj >= 0)
+                        dst[u][v * (EPV / 4) + q] =
+                            ld.f4(a.H + (size_t)jj * R + (v * G + lig) * EPV + 4 * q, true);
+                }
+        }
+    };
+    auto issue_all = [&](int slot_, const int (&j)[K], int bb) {
+        issue(ring[slot_], j, bb);
+        if constexpr (GATHER_H)
+            issue_h(hring[slot_], j, bb);
+    };
 
     load_block(0, jc, sc, ic);
     load_block(1, jn, sn, in_);
 #pragma unroll
     for (int b = 0; b < RING - 1 + REFILL; ++b)
-        issue(ring[b], jc, b);
+        issue_all(b, jc, b);
 
     for (int bk = 0; bk < wblocks; ++bk) {
 #pragma unroll
@@ -155,9 +209,9 @@ __global__ void __launch_bounds__(256, MB) pipe_pass_kernel(const PassArgs a)
                 // batch bb + RING - 1 into the slot that batch bb - 1 freed
                 const int pf = bb + RING - 1;
                 if (pf < BPB)
-                    issue(ring[pf % RING], jc, pf);
+                    issue_all(pf % RING, jc, pf);
                 else
-                    issue(ring[pf % RING], jn, pf - BPB);
+                    issue_all(pf % RING, jn, pf - BPB);
             }
             // use batch bb
             float sv[U];
@@ -166,22 +220,33 @@ __global__ void __launch_bounds__(256, MB) pipe_pass_kernel(const PassArgs a)
             for (int u = 0; u < U; ++u) {
                 const int t = bb * U + u;
                 sv[u] = __shfl_sync(0xffffffffu, sc[t / G], tbase + (t % G));
-                sidx[u] = NZ ? __shfl_sync(0xffffffffu, ic[t / G], tbase + (t % G)) : 0;
+                sidx[u] = (NZ && MODE != M_SDDMM) ? __shfl_sync(0xffffffffu, ic[t / G], tbase + (t % G))
+                                                  : 0;
             }
             float2 y2[U][E2];
+            float2 g2[GATHER_H ? U : 1][GATHER_H ? E2 : 1];
 #pragma unroll
-            for (int u = 0; u < U; ++u)
+            for (int u = 0; u < U; ++u) {
 #pragma unroll
                 for (int v = 0; v < VPL; ++v)
                     unpack2<T>(ring[bb % RING][u][v], &y2[u][v * W2]);
+                if constexpr (GATHER_H) {
+#pragma unroll
+                    for (int q = 0; q < HW; ++q) {
+                        const float4 x = hring[bb % RING][u][q];
+                        g2[u][2 * q] = make_float2(x.x, x.y);
+                        g2[u][2 * q + 1] = make_float2(x.z, x.w);
+                    }
+                }
+            }
             // the slot just read takes batch bb + RING (RING batches ahead;
             // batches past this block come from the next index block)
             if constexpr (REFILL) {
                 const int pf = bb + RING;
                 if (pf < BPB)
-                    issue(ring[bb % RING], jc, pf);
+                    issue_all(bb % RING, jc, pf);
                 else
-                    issue(ring[bb % RING], jn, pf - BPB);
+                    issue_all(bb % RING, jn, pf - BPB);
             }
             if constexpr (MODE == M_SPMM) {
 #pragma unroll
@@ -192,7 +257,9 @@ __global__ void __launch_bounds__(256, MB) pipe_pass_kernel(const PassArgs a)
                         acc2[e] = ffma2(c2, y2[u][e], acc2[e]);
                 }
             } else {
-                float d[U];
+                // d[u] = <L, Y_u>; with two dot products d[U + u] = <H, Y_u>
+                // (over S) or <H_u, L> (over S^T)
+                float d[ND];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     float2 t2 = make_float2(0.f, 0.f);
@@ -200,20 +267,31 @@ __global__ void __launch_bounds__(256, MB) pipe_pass_kernel(const PassArgs a)
                     for (int e = 0; e < E2; ++e)
                         t2 = ffma2(l2[e], y2[u][e], t2);
                     d[u] = t2.x + t2.y;
+                    if constexpr (TWO) {
+                        float2 w2 = make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int e = 0; e < E2; ++e) {
+                            if constexpr (LOCAL_H)
+                                w2 = ffma2(h2[e], y2[u][e], w2);
+                            else
+                                w2 = ffma2(g2[u][e], l2[e], w2);
+                        }
+                        d[U + u] = w2.x + w2.y;
+                    }
                 }
                 // sum over the G lanes of the group, two dot products per step
 #pragma unroll
                 for (int off = G / 2; off > 0; off >>= 1) {
 #pragma unroll
-                    for (int u = 0; u + 1 < U; u += 2) {
-                        const float2 o = make_float2(__shfl_xor_sync(0xffffffffu, d[u], off),
-                                                     __shfl_xor_sync(0xffffffffu, d[u + 1], off));
-                        const float2 s2 = fadd2(make_float2(d[u], d[u + 1]), o);
-                        d[u] = s2.x;
-                        d[u + 1] = s2.y;
+                    for (int i = 0; i + 1 < ND; i += 2) {
+                        const float2 o = make_float2(__shfl_xor_sync(0xffffffffu, d[i], off),
+                                                     __shfl_xor_sync(0xffffffffu, d[i + 1], off));
+                        const float2 s2 = fadd2(make_float2(d[i], d[i + 1]), o);
+                        d[i] = s2.x;
+                        d[i + 1] = s2.y;
                     }
-                    if constexpr (U % 2)
-                        d[U - 1] += __shfl_xor_sync(0xffffffffu, d[U - 1], off);
+                    if constexpr (ND % 2)
+                        d[ND - 1] += __shfl_xor_sync(0xffffffffu, d[ND - 1], off);
                 }
                 if constexpr (MODE == M_FUSED) {
 #pragma unroll
@@ -224,13 +302,42 @@ __global__ void __launch_bounds__(256, MB) pipe_pass_kernel(const PassArgs a)
                         for (int e = 0; e < E2; ++e)
                             acc2[e] = ffma2(c2, y2[u][e], acc2[e]);
                     }
-                } else {   // M_SDDMM
+                } else if constexpr (MODE == M_SDDMM) {
 #pragma unroll
-                    for (int u = 0; u < U; ++u)
-                        if (sidx[u] >= 0 && lig == (u % G))
-                            a.nzout[sidx[u]] = sv[u] * d[u];
+                    for (int u = 0; u < U; ++u) {
+                        const int t = bb * U + u;
+                        if (lig == t % G)
+                            held[t / G] = sv[u] * d[u];
+                    }
+                } else if constexpr (MODE == M_BWD_ROW) {
+                    // ds = <A_i, B_j> <G_i, B_j>;  dA_i += s <G_i, B_j> B_j
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        if (a.nzout && sidx[u] >= 0 && lig == (u % G))
+                            a.nzout[sidx[u]] = d[u] * d[U + u];
+                        const float c = sv[u] * d[U + u];
+                        const float2 c2 = make_float2(c, c);
+#pragma unroll
+                        for (int e = 0; e < E2; ++e)
+                            acc2[e] = ffma2(c2, y2[u][e], acc2[e]);
+                    }
+                } else {   // M_BWD_COL: dB_j += s (<A_i, B_j> G_i + <G_i, B_j> A_i)
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const float c1 = sv[u] * d[u], c2s = sv[u] * d[U + u];
+                        const float2 c1v = make_float2(c1, c1), c2v = make_float2(c2s, c2s);
+#pragma unroll
+                        for (int e = 0; e < E2; ++e)
+                            acc2[e] = ffma2(c1v, g2[u][e], ffma2(c2v, y2[u][e], acc2[e]));
+                    }
                 }
             }
+        }
+        if constexpr (MODE == M_SDDMM) {
+#pragma unroll
+            for (int e = 0; e < K; ++e)
+                if (ic[e] >= 0)
+                    a.nzout[ic[e]] = held[e];
         }
         // the next block becomes current; fetch the one after it
 #pragma unroll

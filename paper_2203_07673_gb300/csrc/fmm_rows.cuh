@@ -272,8 +272,16 @@ __device__ __forceinline__ void team_pass_body(const PassArgs &a, long long gid,
 
     constexpr int PER = NG * U;
     constexpr bool NZ = MODE == M_SDDMM || MODE == M_BWD_ROW;
-    // one batch: the gathers of its U nonzeros per group, then their use
-    auto batch = [&](const int (&jj)[U], const int (&sidx)[U], const float (&sv)[U]) {
+    // Per-nonzero outputs (v, ds).  With one group per team and the team's
+    // index blocks, the lane that loaded a nonzero's index keeps its value
+    // (owner == the nonzero's position in the block) and the team stores a
+    // block of values at once (HOLD); otherwise each value is stored as it
+    // is computed.
+    constexpr bool HOLD = NZ && NG == 1 && TEAM % PER == 0;
+    float held = 0.f;
+    // one batch: the gathers of its U nonzeros per group, then their use;
+    // `first` is the position in the team's index block of its nonzero 0
+    auto batch = [&](const int (&jj)[U], const int (&sidx)[U], const float (&sv)[U], int first) {
         float y[U][E];
         float h[MODE == M_BWD_COL ? U : 1][E];
 #pragma unroll
@@ -332,11 +340,19 @@ __device__ __forceinline__ void team_pass_body(const PassArgs &a, long long gid,
                     for (int e = 0; e < E; ++e)
                         acc[e] = fmaf(c, y[u][e], acc[e]);
                 } else if constexpr (MODE == M_SDDMM) {
-                    if (lig == (u % G))
+                    if constexpr (HOLD) {
+                        if ((lane & (TEAM - 1)) == first + u)
+                            held = sv[u] * d[u];
+                    } else if (lig == (u % G)) {
                         a.nzout[sidx[u]] = sv[u] * d[u];
+                    }
                 } else if constexpr (MODE == M_BWD_ROW) {
-                    if (a.nzout && lig == (u % G))
+                    if constexpr (HOLD) {
+                        if ((lane & (TEAM - 1)) == first + u)
+                            held = d[u] * d[U + u];
+                    } else if (a.nzout && lig == (u % G)) {
                         a.nzout[sidx[u]] = d[u] * d[U + u];
+                    }
                     const float c = sv[u] * d[U + u];
 #pragma unroll
                     for (int e = 0; e < E; ++e)
@@ -381,10 +397,14 @@ __device__ __forceinline__ void team_pass_body(const PassArgs &a, long long gid,
                     const int src = tbase + sub * PER + u * NG + grp;
                     jj[u] = __shfl_sync(0xffffffffu, myj, src);
                     sv[u] = __shfl_sync(0xffffffffu, mys, src);
-                    sidx[u] = NZ ? __shfl_sync(0xffffffffu, mysi, src) : 0;
+                    sidx[u] = (NZ && !HOLD) ? __shfl_sync(0xffffffffu, mysi, src) : 0;
                 }
-                batch(jj, sidx, sv);
+                batch(jj, sidx, sv, sub * PER);
             }
+            // the block's per-nonzero outputs, one store per lane
+            if constexpr (HOLD)
+                if (q < end && a.nzout)
+                    a.nzout[mysi] = held;
         }
     } else {
         const int iters = (end - beg + PER - 1) / PER;
@@ -404,7 +424,7 @@ __device__ __forceinline__ void team_pass_body(const PassArgs &a, long long gid,
                     jj[u] = -1; sidx[u] = 0; sv[u] = 0.f;
                 }
             }
-            batch(jj, sidx, sv);
+            batch(jj, sidx, sv, 0);
         }
     }
 
