@@ -265,6 +265,20 @@ int fmm_fusedmm_t_bwd(const fmm_plan *plan, const float *vals, const void *A,
                       float *ds, fmm_stream stream);
 
 /*
+ * Accumulating forms, the "+=" of the distributed algorithms (Algorithm 1:
+ * each phase adds the contribution of one column block of S to the rows it
+ * owns): out_m += FusedMMA, out_n += FusedMMB, dA += and dB += the adjoint
+ * of FusedMMA (ds, per nonzero, is overwritten).  The output buffers must
+ * hold valid float32 values; otherwise as the plain calls.
+ */
+int fmm_fusedmm_acc(const fmm_plan *plan, const float *vals, const void *A, const void *B,
+                    float *out_m, fmm_stream stream);
+int fmm_fusedmm_t_acc(const fmm_plan *plan, const float *vals, const void *A, const void *B,
+                      float *out_n, fmm_stream stream);
+int fmm_fusedmm_bwd_acc(const fmm_plan *plan, const float *vals, const void *A, const void *B,
+                        const float *G, float *dA, float *dB, float *ds, fmm_stream stream);
+
+/*
  * Kernel variant of a plan's row passes (the codes of
  * fmm_plan_options.variant; 0 leaves a side unchanged).  variant applies to
  * passes over S, variant_t to passes over S^T.  Used by the autotuner; calls

@@ -179,7 +179,8 @@ int need_t(const fmm_plan *p)
 }
 
 int run_pass(const fmm_plan *p, const Side &side, int mode, const float *s, const void *L,
-             const void *Y, const float *H, float *out, float *nzout, cudaStream_t st)
+             const void *Y, const float *H, float *out, float *nzout, cudaStream_t st,
+             bool accumulate = false)
 {
     PassArgs a;
     a.row_ptr = side.row_ptr;
@@ -199,6 +200,7 @@ int run_pass(const fmm_plan *p, const Side &side, int mode, const float *s, cons
     a.nzout = nzout;
     a.r = p->r;
     a.err = p->err;
+    a.accumulate = accumulate ? 1 : 0;
     cudaError_t e = cudaSuccess;
     if (side.perm && s) {
         if (s == p->static_src && p->vals_static) {
@@ -215,7 +217,7 @@ int run_pass(const fmm_plan *p, const Side &side, int mode, const float *s, cons
     if (e == cudaSuccess)
         e = launch_pass(mode, p->dtype, side.variant, a, st);
     if (e == cudaSuccess && mode != M_SDDMM)
-        e = launch_combine(side, out, p->r, st);
+        e = launch_combine(side, out, p->r, accumulate, st);
     if (e != cudaSuccess) {
         set_error("kernel launch", e);
         return FMM_ECUDA;
@@ -359,19 +361,19 @@ int fmm_spmm_t(const fmm_plan *p, const float *v, const void *A, float *out_n, f
                     (cudaStream_t)stream);
 }
 
-int fmm_fusedmm(const fmm_plan *p, const float *vals, const void *A, const void *B, float *out_m,
-                fmm_stream stream)
+static int fusedmm_a(const fmm_plan *p, const float *vals, const void *A, const void *B,
+                     float *out_m, fmm_stream stream, bool acc)
 {
     CHECK(check_plan(p));
     CHECK(need(A, p->m, "A"));
     CHECK(need(B, p->n, "B"));
     CHECK(need(out_m, p->m, "out_m"));
     return run_pass(p, p->rows, M_FUSED, vals, A, B, nullptr, out_m, nullptr,
-                    (cudaStream_t)stream);
+                    (cudaStream_t)stream, acc);
 }
 
-int fmm_fusedmm_t(const fmm_plan *p, const float *vals, const void *A, const void *B,
-                  float *out_n, fmm_stream stream)
+static int fusedmm_b(const fmm_plan *p, const float *vals, const void *A, const void *B,
+                     float *out_n, fmm_stream stream, bool acc)
 {
     CHECK(check_plan(p));
     CHECK(need_t(p));
@@ -379,11 +381,12 @@ int fmm_fusedmm_t(const fmm_plan *p, const float *vals, const void *A, const voi
     CHECK(need(B, p->n, "B"));
     CHECK(need(out_n, p->n, "out_n"));
     return run_pass(p, p->cols, M_FUSED, vals, B, A, nullptr, out_n, nullptr,
-                    (cudaStream_t)stream);
+                    (cudaStream_t)stream, acc);
 }
 
-int fmm_fusedmm_bwd(const fmm_plan *p, const float *vals, const void *A, const void *B,
-                    const float *G, float *dA, float *dB, float *ds, fmm_stream stream)
+static int fusedmm_a_bwd(const fmm_plan *p, const float *vals, const void *A, const void *B,
+                         const float *G, float *dA, float *dB, float *ds, fmm_stream stream,
+                         bool acc)
 {
     CHECK(check_plan(p));
     CHECK(need(A, p->m, "A"));
@@ -393,10 +396,46 @@ int fmm_fusedmm_bwd(const fmm_plan *p, const float *vals, const void *A, const v
         CHECK(need_t(p));
     cudaStream_t st = (cudaStream_t)stream;
     if (dA || ds)
-        CHECK(run_pass(p, p->rows, M_BWD_ROW, vals, A, B, G, dA, ds, st));
+        CHECK(run_pass(p, p->rows, M_BWD_ROW, vals, A, B, G, dA, ds, st, acc));
     if (dB)
-        CHECK(run_pass(p, p->cols, M_BWD_COL, vals, B, A, G, dB, nullptr, st));
+        CHECK(run_pass(p, p->cols, M_BWD_COL, vals, B, A, G, dB, nullptr, st, acc));
     return FMM_OK;
+}
+
+int fmm_fusedmm(const fmm_plan *p, const float *vals, const void *A, const void *B, float *out_m,
+                fmm_stream stream)
+{
+    return fusedmm_a(p, vals, A, B, out_m, stream, false);
+}
+
+int fmm_fusedmm_t(const fmm_plan *p, const float *vals, const void *A, const void *B,
+                  float *out_n, fmm_stream stream)
+{
+    return fusedmm_b(p, vals, A, B, out_n, stream, false);
+}
+
+int fmm_fusedmm_bwd(const fmm_plan *p, const float *vals, const void *A, const void *B,
+                    const float *G, float *dA, float *dB, float *ds, fmm_stream stream)
+{
+    return fusedmm_a_bwd(p, vals, A, B, G, dA, dB, ds, stream, false);
+}
+
+int fmm_fusedmm_acc(const fmm_plan *p, const float *vals, const void *A, const void *B,
+                    float *out_m, fmm_stream stream)
+{
+    return fusedmm_a(p, vals, A, B, out_m, stream, true);
+}
+
+int fmm_fusedmm_t_acc(const fmm_plan *p, const float *vals, const void *A, const void *B,
+                      float *out_n, fmm_stream stream)
+{
+    return fusedmm_b(p, vals, A, B, out_n, stream, true);
+}
+
+int fmm_fusedmm_bwd_acc(const fmm_plan *p, const float *vals, const void *A, const void *B,
+                        const float *G, float *dA, float *dB, float *ds, fmm_stream stream)
+{
+    return fusedmm_a_bwd(p, vals, A, B, G, dA, dB, ds, stream, true);
 }
 
 int fmm_fusedmm_t_bwd(const fmm_plan *p, const float *vals, const void *A, const void *B,

@@ -104,8 +104,9 @@ struct PassArgs {
     float *out;                // rows x r (NULL: not stored)
     float *nzout;              // per-nonzero output in S order (NULL: none)
     int32_t r;
-    int32_t *err;              // device word set to 1 by a pass that gave up a
+    int32_t *err = nullptr;    // device word set to 1 by a pass that gave up a
                                // bounded wait (NULL: not reported)
+    int32_t accumulate = 0;    // 1: out += the pass's rows (else out =)
 };
 
 // Launches one row pass (main kernel; the combine kernel for split rows is
@@ -143,8 +144,9 @@ cudaError_t launch_values_t(const fmm_plan *p, const float *src, float *dst, cud
 // S^T slots per window of the windowed permutation (32 MB of float32 values:
 // a window's staging values stay in L2 while its slots are filled).
 constexpr int64_t kPermuteWindow = int64_t(1) << 23;
-// Sums the partial rows of every split row, in chunk order, into out.
-cudaError_t launch_combine(const Side &side, float *out, int32_t r,
+// Sums the partial rows of every split row, in chunk order, into out (added
+// to out's rows when accumulate is set).
+cudaError_t launch_combine(const Side &side, float *out, int32_t r, bool accumulate,
                            cudaStream_t st);
 
 bool fast_r(int32_t r);

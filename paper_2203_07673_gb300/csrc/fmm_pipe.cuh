@@ -358,7 +358,8 @@ __global__ void __launch_bounds__(256, MB) pipe_pass_kernel(const PassArgs a)
                     for (int w = 0; w < W2; w += 2) {
                         const int k = (v * G + lig) * EPV + 2 * w;
                         const float2 p0 = acc2[v * W2 + w], p1 = acc2[v * W2 + w + 1];
-                        ld.st4(dst + k, make_float4(p0.x, p0.y, p1.x, p1.y));
+                        out_store4(ld, dst + k, make_float4(p0.x, p0.y, p1.x, p1.y),
+                                   a.accumulate && slot < 0);
                     }
                 }
             }

@@ -768,7 +768,7 @@ cudaError_t launch_values_t(const fmm_plan *p, const float *src, float *dst, cud
 }
 
 __global__ void combine_kernel(const int4 *split, int32_t n_split, const float *partials,
-                               float *out, int32_t r)
+                               float *out, int32_t r, int32_t accumulate)
 {
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -779,16 +779,18 @@ __global__ void combine_kernel(const int4 *split, int32_t n_split, const float *
         float acc = 0.f;
         for (int c = 0; c < sp.z; ++c)
             acc += partials[(size_t)(sp.y + c) * r + k];
-        out[(size_t)sp.x * r + k] = acc;
+        out[(size_t)sp.x * r + k] = accumulate ? out[(size_t)sp.x * r + k] + acc : acc;
     }
 }
 
-cudaError_t launch_combine(const Side &side, float *out, int32_t r, cudaStream_t st)
+cudaError_t launch_combine(const Side &side, float *out, int32_t r, bool accumulate,
+                           cudaStream_t st)
 {
     if (side.n_split == 0 || !out)
         return cudaSuccess;
     combine_kernel<<<(side.n_split + 7) / 8, 256, 0, st>>>(side.split, side.n_split,
-                                                           side.partials, out, r);
+                                                           side.partials, out, r,
+                                                           accumulate ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -210,9 +210,20 @@ __device__ __forceinline__ void team_load_f32(const Loader &ld, const float *row
     }
 }
 
+// Stores four output elements; with add, adds them to what the row holds
+// (the accumulating calls: out += the pass).
+__device__ __forceinline__ void out_store4(const Loader &ld, float *p, float4 v, bool add)
+{
+    if (add) {
+        const float4 o = __ldcs(reinterpret_cast<const float4 *>(p));
+        v.x += o.x; v.y += o.y; v.z += o.z; v.w += o.w;
+    }
+    ld.st4(p, v);
+}
+
 template <typename T, int VPL, int G>
 __device__ __forceinline__ void team_store_f32(const Loader &ld, float *row, int lig,
-                                               const float *f)
+                                               const float *f, bool add = false)
 {
     constexpr int EPV = Elem<T>::PER16;
 #pragma unroll
@@ -220,8 +231,8 @@ __device__ __forceinline__ void team_store_f32(const Loader &ld, float *row, int
 #pragma unroll
         for (int q = 0; q < EPV / 4; ++q) {
             const int e = v * EPV + 4 * q;
-            ld.st4(row + (v * G + lig) * EPV + 4 * q,
-                   make_float4(f[e + 0], f[e + 1], f[e + 2], f[e + 3]));
+            out_store4(ld, row + (v * G + lig) * EPV + 4 * q,
+                       make_float4(f[e + 0], f[e + 1], f[e + 2], f[e + 3]), add);
         }
     }
 }
@@ -440,7 +451,7 @@ __device__ __forceinline__ void team_pass_body(const PassArgs &a, long long gid,
             float *dst = slot >= 0 ? a.partials + (size_t)slot * R
                                    : (a.out ? a.out + (size_t)row * R : nullptr);
             if (dst)
-                team_store_f32<T, VPL, G>(ld, dst, lig, acc);
+                team_store_f32<T, VPL, G>(ld, dst, lig, acc, a.accumulate && slot < 0);
         }
     }
 }
@@ -509,7 +520,8 @@ __global__ void __launch_bounds__(256) row_pass_generic(const PassArgs a)
     if (ACC)
         dst = slot >= 0 ? a.partials + (size_t)slot * r
                         : (a.out ? a.out + (size_t)row * r : nullptr);
-    if (dst)
+    // the accumulating calls add into the output row as it stands
+    if (dst && !(a.accumulate && slot < 0))
         for (int k = lane; k < r; k += 32)
             dst[k] = 0.f;
     const T *Li = L ? L + (size_t)row * r : nullptr;

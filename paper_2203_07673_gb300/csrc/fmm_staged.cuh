@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(256) staged_pass_kernel(const PassArgs a)
             float *dst = slot >= 0 ? a.partials + (size_t)slot * R
                                    : (a.out ? a.out + (size_t)row * R : nullptr);
             if (dst)
-                team_store_f32<T, VPL, G>(ld, dst, lig, acc);
+                team_store_f32<T, VPL, G>(ld, dst, lig, acc, a.accumulate && slot < 0);
         }
     }
 }

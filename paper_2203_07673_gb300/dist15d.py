@@ -1,0 +1,245 @@
+"""1.5D dense-shifting FusedMM with local kernel fusion (Sec. V, Algorithm 1, c = 1).
+
+p ranks in one ring (a p x 1 grid: replication factor c = 1).  Rank k owns
+  * a block of rows of S (R_k, balanced by nonzeros), the same rows of A and of
+    the FusedMMA output,
+  * one block of columns of S = rows of B (C_k, n / p rows each) and the same
+    rows of the FusedMMB output.
+Its rows of S are cut by column block into p local patterns S_{k,l}, each with
+its own plan.  A FusedMMA runs p phases: in phase t rank k holds B block
+l = (k + t) mod p, adds FusedMMA(S_{k,l}, A_k, B_l) to its output rows
+(local kernel fusion: the SDDMM values stay in registers, one round of shifts
+serves both halves, Sec. V "Local Kernel Fusion") and passes B_l to rank
+k - 1 while the next block arrives from k + 1; the shift of the next block is
+posted before the phase's kernel, so it overlaps it.  FusedMMB and the B
+gradient follow Algorithm 1's SpMMB mode: the output block travels with its B
+block, every rank adds its contribution, and after p phases and p shifts the
+block is back at its owner.  The A gradient stays local (like FusedMMA), ds
+is per nonzero.
+
+This module holds index arithmetic and the schedule only.  The local work is
+done by `ops` (default: the library's kernels through fmm: plans over
+S_{k,l}, fmm_fusedmm_acc, fmm_fusedmm_t_acc, fmm_fusedmm_bwd_acc); the
+shifts by torch.distributed point-to-point calls (NCCL moves device tensors;
+with gloo the blocks are staged through host memory).  No kernel is handed
+another rank's memory.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+import torch.distributed as dist
+
+
+def row_bounds_by_nnz(row_ptr, parts: int) -> np.ndarray:
+    """Row block boundaries (parts + 1 entries) splitting the rows of a CSR
+    into `parts` consecutive blocks of about nnz / parts nonzeros each."""
+    rp = np.asarray(row_ptr, dtype=np.int64)
+    m = rp.shape[0] - 1
+    nnz = int(rp[-1])
+    targets = [(k * nnz) // parts for k in range(parts + 1)]
+    bounds = np.searchsorted(rp, targets, side="left").astype(np.int64)
+    bounds[0], bounds[-1] = 0, m
+    return bounds
+
+
+def col_bounds_uniform(n: int, parts: int) -> np.ndarray:
+    """Column block boundaries (parts + 1 entries): blocks of n / parts."""
+    return np.array([(l * n) // parts for l in range(parts + 1)], dtype=np.int64)
+
+
+def split_by_column_blocks(row_ptr: torch.Tensor, col_idx: torch.Tensor, col_bounds):
+    """The local pattern of each column block of a row block's CSR.
+
+    row_ptr (rows + 1) and col_idx (nnz) are int32 tensors with global column
+    indices.  Returns a list with one entry per block l:
+    (row_ptr_l int32, col_idx_l int32 (columns relative to the block start),
+    slots_l int64: the position in the input CSR of each nonzero of S_l)."""
+    dev = col_idx.device
+    rows = row_ptr.numel() - 1
+    nnz = col_idx.numel()
+    deg = (row_ptr[1:] - row_ptr[:-1]).long()
+    row_of = torch.repeat_interleave(torch.arange(rows, device=dev), deg)
+    cb = torch.as_tensor(np.asarray(col_bounds, dtype=np.int64), device=dev)
+    block = torch.searchsorted(cb, col_idx.long(), right=True) - 1
+    # stable order by (block, row); within a row the input order is kept
+    key = block * (rows + 1) + row_of
+    order = torch.sort(key, stable=True).indices
+    out = []
+    counts = torch.bincount(block, minlength=len(col_bounds) - 1).tolist()
+    start = 0
+    for l, c in enumerate(counts):
+        sel = order[start:start + c]
+        start += c
+        rp = torch.zeros(rows + 1, dtype=torch.int64, device=dev)
+        if c:
+            rp[1:] = torch.cumsum(torch.bincount(row_of[sel], minlength=rows), 0)
+        ci = (col_idx[sel].long() - int(col_bounds[l])).to(torch.int32)
+        out.append((rp.to(torch.int32), ci, sel))
+    assert start == nnz
+    return out
+
+
+class LibraryOps:
+    """Local kernels of the library (fmm): one plan per local pattern."""
+
+    def __init__(self):
+        from . import fmm
+        self.fmm = fmm
+
+    def plan(self, row_ptr, col_idx, n, r, dtype):
+        return self.fmm.Plan(row_ptr, col_idx, n, r, dtype)
+
+    def fusedmm_acc(self, plan, vals, A, B, out):
+        self.fmm.fusedmm_acc(plan, vals, A, B, out)
+
+    def fusedmm_t_acc(self, plan, vals, A, B, out):
+        self.fmm.fusedmm_t_acc(plan, vals, A, B, out)
+
+    def fusedmm_bwd_acc(self, plan, vals, A, B, G, dA, dB, ds):
+        self.fmm.fusedmm_bwd_acc(plan, vals, A, B, G, dA, dB, ds)
+
+    def close(self, plan):
+        plan.close()
+
+
+class FusedMM15D:
+    """FusedMMA, FusedMMB and the FusedMMA adjoint of one distributed S.
+
+    Every rank of `group` calls every method with its own blocks:
+      row_ptr, col_idx  its rows of S (int32, global column indices)
+      n, r, dtype       global columns of S, dense width, dense dtype
+      col_bounds        column block boundaries (default: n / p each)
+    A_k is (rows, r) and B_k (cols of block k, r), both of `dtype`; vals_k
+    (nnz of the rank's rows, float32, rank-local CSR order) or None (all
+    ones).  Outputs are float32."""
+
+    def __init__(self, row_ptr, col_idx, n, r, dtype=torch.float32, group=None, col_bounds=None,
+                 ops=None):
+        self.group = group
+        self.p = dist.get_world_size(group)
+        self.k = dist.get_rank(group)
+        self.n, self.r, self.dtype = int(n), int(r), dtype
+        self.col_bounds = (col_bounds_uniform(self.n, self.p) if col_bounds is None
+                           else np.asarray(col_bounds, dtype=np.int64))
+        self.rows = row_ptr.numel() - 1
+        self.nnz = col_idx.numel()
+        self.ops = ops if ops is not None else LibraryOps()
+        self.blocks = split_by_column_blocks(row_ptr, col_idx, self.col_bounds)
+        widths = np.diff(self.col_bounds)
+        self.maxw = int(widths.max()) if len(widths) else 0
+        self.plans = [self.ops.plan(rp, ci, int(widths[l]), self.r, dtype)
+                      for l, (rp, ci, _) in enumerate(self.blocks)]
+        self.device = col_idx.device
+
+    def close(self):
+        for pl in self.plans:
+            self.ops.close(pl)
+        self.plans = []
+
+    # ------------------------------------------------------------ schedule
+
+    def block_of_phase(self, t: int) -> int:
+        """The B block rank k holds in phase t."""
+        return (self.k + t) % self.p
+
+    def _width(self, l):
+        return int(self.col_bounds[l + 1] - self.col_bounds[l])
+
+    def _vals(self, vals, l):
+        return None if vals is None else vals.index_select(0, self.blocks[l][2])
+
+    def _padded(self, X, dtype):
+        buf = torch.zeros((self.maxw, self.r), dtype=dtype, device=X.device)
+        buf[:X.shape[0]].copy_(X)
+        return buf
+
+    def _shift(self, send, recv):
+        """send -> rank k - 1, recv <- rank k + 1 (returns a waitable)."""
+        dst = (self.k - 1) % self.p
+        src = (self.k + 1) % self.p
+        if self.p == 1:
+            recv.copy_(send)
+            return []
+        host = dist.get_backend(self.group) == "gloo" and send.is_cuda
+        if host:
+            s_h, r_h = send.cpu(), torch.empty(recv.shape, dtype=recv.dtype)
+            reqs = dist.batch_isend_irecv([
+                dist.P2POp(dist.isend, s_h, self._global(dst), group=self.group),
+                dist.P2POp(dist.irecv, r_h, self._global(src), group=self.group)])
+            return [(reqs, r_h, recv)]
+        reqs = dist.batch_isend_irecv([
+            dist.P2POp(dist.isend, send, self._global(dst), group=self.group),
+            dist.P2POp(dist.irecv, recv, self._global(src), group=self.group)])
+        return [(reqs, None, None)]
+
+    def _global(self, rank):
+        return rank if self.group is None else dist.get_global_rank(self.group, rank)
+
+    @staticmethod
+    def _wait(handles):
+        for reqs, r_h, recv in handles:
+            for q in reqs:
+                q.wait()
+            if r_h is not None:
+                recv.copy_(r_h)
+
+    # ------------------------------------------------------------ operations
+
+    def fusedmm(self, vals, A_k, B_k):
+        """FusedMMA rows of this rank: out_i = sum_j s_ij <A_i, B_j> B_j."""
+        out = torch.zeros((self.rows, self.r), dtype=torch.float32, device=A_k.device)
+        bufs = [self._padded(B_k, self.dtype), torch.empty((self.maxw, self.r), dtype=self.dtype,
+                                                            device=A_k.device)]
+        cur = 0
+        for t in range(self.p):
+            l = self.block_of_phase(t)
+            # the next block is in flight while this phase computes
+            pend = self._shift(bufs[cur], bufs[1 - cur]) if t + 1 < self.p else []
+            self.ops.fusedmm_acc(self.plans[l], self._vals(vals, l), A_k,
+                                 bufs[cur][:self._width(l)], out)
+            self._wait(pend)
+            cur = 1 - cur
+        return out
+
+    def fusedmm_t(self, vals, A_k, B_k):
+        """FusedMMB rows of this rank's B block: out_j = sum_i s_ij <A_i, B_j> A_i."""
+        bufs = [self._padded(B_k, self.dtype), torch.empty((self.maxw, self.r), dtype=self.dtype,
+                                                            device=A_k.device)]
+        outs = [torch.zeros((self.maxw, self.r), dtype=torch.float32, device=A_k.device),
+                torch.empty((self.maxw, self.r), dtype=torch.float32, device=A_k.device)]
+        cur = 0
+        for t in range(self.p):
+            l = self.block_of_phase(t)
+            pend = self._shift(bufs[cur], bufs[1 - cur]) if t + 1 < self.p else []
+            w = self._width(l)
+            self.ops.fusedmm_t_acc(self.plans[l], self._vals(vals, l), A_k, bufs[cur][:w],
+                                   outs[cur][:w])
+            # the output block travels on with its B block
+            self._wait(pend + self._shift(outs[cur], outs[1 - cur]))
+            cur = 1 - cur
+        return outs[cur][:self._width(self.k)].clone()
+
+    def fusedmm_bwd(self, vals, A_k, B_k, G_k):
+        """Adjoint of FusedMMA for L = <G, FusedMMA>: (dA rows of this rank,
+        dB rows of this rank's B block, ds of this rank's nonzeros)."""
+        dev = A_k.device
+        dA = torch.zeros((self.rows, self.r), dtype=torch.float32, device=dev)
+        ds = torch.zeros(self.nnz, dtype=torch.float32, device=dev)
+        bufs = [self._padded(B_k, self.dtype), torch.empty((self.maxw, self.r), dtype=self.dtype,
+                                                            device=dev)]
+        dBs = [torch.zeros((self.maxw, self.r), dtype=torch.float32, device=dev),
+               torch.empty((self.maxw, self.r), dtype=torch.float32, device=dev)]
+        cur = 0
+        for t in range(self.p):
+            l = self.block_of_phase(t)
+            pend = self._shift(bufs[cur], bufs[1 - cur]) if t + 1 < self.p else []
+            w = self._width(l)
+            sel = self.blocks[l][2]
+            ds_l = torch.empty(sel.numel(), dtype=torch.float32, device=dev)
+            self.ops.fusedmm_bwd_acc(self.plans[l], self._vals(vals, l), A_k, bufs[cur][:w], G_k,
+                                     dA, dBs[cur][:w], ds_l)
+            ds.index_copy_(0, sel, ds_l)
+            self._wait(pend + self._shift(dBs[cur], dBs[1 - cur]))
+            cur = 1 - cur
+        return dA, dBs[cur][:self._width(self.k)].clone(), ds

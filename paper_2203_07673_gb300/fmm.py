@@ -38,6 +38,9 @@ _SIGNATURES = {
     "fmm_fusedmm_t": ([_P, _P, _P, _P, _P, _P], ctypes.c_int),
     "fmm_fusedmm_bwd": ([_P, _P, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "fmm_fusedmm_t_bwd": ([_P, _P, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
+    "fmm_fusedmm_acc": ([_P, _P, _P, _P, _P, _P], ctypes.c_int),
+    "fmm_fusedmm_t_acc": ([_P, _P, _P, _P, _P, _P], ctypes.c_int),
+    "fmm_fusedmm_bwd_acc": ([_P, _P, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "fmm_fusedmm_noalloc": ([_P, _I32, _I32, _P, _P, _P, _P, _P], ctypes.c_int),
     "fmm_plan_set_variant": ([_P, _I32, _I32], ctypes.c_int),
     "fmm_plan_set_values": ([_P, _P, _P], ctypes.c_int),
@@ -295,6 +298,37 @@ def fusedmm_bwd(plan: Plan, vals, A, B, G, need=(True, True, True), stream=None)
                                plan._f32(dB, (plan.n, plan.r), "dB"),
                                plan._f32(ds, (plan.nnz,), "ds"), _stream(stream))
     _check(rc, "fmm_fusedmm_bwd")
+    return dA, dB, ds
+
+
+def fusedmm_acc(plan: Plan, vals, A, B, out, stream=None):
+    """fmm_fusedmm_acc: out += FusedMMA (out float32, m x r, valid values)."""
+    rc = lib().fmm_fusedmm_acc(plan.handle, plan._f32(vals, (plan.nnz,), "vals"),
+                               plan._dense(A, plan.m, "A"), plan._dense(B, plan.n, "B"),
+                               plan._f32(out, (plan.m, plan.r), "out"), _stream(stream))
+    _check(rc, "fmm_fusedmm_acc")
+    return out
+
+
+def fusedmm_t_acc(plan: Plan, vals, A, B, out, stream=None):
+    """fmm_fusedmm_t_acc: out += FusedMMB (out float32, n x r, valid values)."""
+    rc = lib().fmm_fusedmm_t_acc(plan.handle, plan._f32(vals, (plan.nnz,), "vals"),
+                                 plan._dense(A, plan.m, "A"), plan._dense(B, plan.n, "B"),
+                                 plan._f32(out, (plan.n, plan.r), "out"), _stream(stream))
+    _check(rc, "fmm_fusedmm_t_acc")
+    return out
+
+
+def fusedmm_bwd_acc(plan: Plan, vals, A, B, G, dA=None, dB=None, ds=None, stream=None):
+    """fmm_fusedmm_bwd_acc: dA += and dB += the adjoint of FusedMMA, ds =
+    (each may be None to skip it)."""
+    rc = lib().fmm_fusedmm_bwd_acc(plan.handle, plan._f32(vals, (plan.nnz,), "vals"),
+                                   plan._dense(A, plan.m, "A"), plan._dense(B, plan.n, "B"),
+                                   plan._f32(G, (plan.m, plan.r), "G"),
+                                   plan._f32(dA, (plan.m, plan.r), "dA"),
+                                   plan._f32(dB, (plan.n, plan.r), "dB"),
+                                   plan._f32(ds, (plan.nnz,), "ds"), _stream(stream))
+    _check(rc, "fmm_fusedmm_bwd_acc")
     return dA, dB, ds
 
 

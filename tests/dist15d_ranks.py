@@ -1,0 +1,100 @@
+"""Rank bodies of the 1.5D FusedMM tests (Sec. V, Algorithm 1, c = 1), run in
+spawned processes by tests/test_dist15d.py and tests/test_gpu_dist15d.py.
+
+Every rank draws the same seeded whole problem, keeps its own row block of S
+and A and its own block of B, runs FusedMMA, FusedMMB and the FusedMMA
+adjoint through paper_2203_07673_gb300.dist15d, and returns its blocks of
+the results; the parent assembles them and compares them with the oracle on
+the whole matrix.  `OracleOps` is the local-kernel stand-in of the CPU test:
+it evaluates each local call with the FP64 oracle (test infrastructure; the
+product never imports the oracle)."""
+import os
+import sys
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+sys.path.insert(0, os.path.join(ROOT, "tests"))
+
+
+def problem(seed, m=300, n=250, r=32):
+    from paper_2203_07673_gb300 import workloads as wl
+    rng = np.random.default_rng(seed)
+    S = wl.random_csr(m, n, rng, mean_deg=6, empty_frac=0.1, hubs=((7, 180), (m - 1, 90)))
+    vals = rng.uniform(0.5, 1.5, S.nnz).astype(np.float32)
+    A = (rng.standard_normal((m, r)) / np.sqrt(r)).astype(np.float32)
+    B = (rng.standard_normal((n, r)) / np.sqrt(r)).astype(np.float32)
+    G = rng.standard_normal((m, r)).astype(np.float32)
+    return S, vals, A, B, G
+
+
+class OracleOps:
+    """Local calls of the 1.5D driver evaluated by the FP64 oracle (CPU)."""
+
+    def __init__(self):
+        import oracle
+        self.o = oracle
+
+    def plan(self, row_ptr, col_idx, n, r, dtype):
+        return dict(rp=row_ptr.cpu().numpy(), ci=col_idx.cpu().numpy(), n=int(n))
+
+    @staticmethod
+    def _np(x):
+        return None if x is None else x.detach().cpu().double().numpy()
+
+    def fusedmm_acc(self, plan, vals, A, B, out):
+        res = self.o.fusedmm(plan["rp"], plan["ci"], self._np(vals), self._np(A), self._np(B),
+                             plan["n"])
+        out += torch.from_numpy(res).to(out.dtype)
+
+    def fusedmm_t_acc(self, plan, vals, A, B, out):
+        res = self.o.fusedmm_t(plan["rp"], plan["ci"], self._np(vals), self._np(A), self._np(B),
+                               plan["n"])
+        out += torch.from_numpy(res).to(out.dtype)
+
+    def fusedmm_bwd_acc(self, plan, vals, A, B, G, dA, dB, ds):
+        ga, gb, gs = self.o.fusedmm_grad(plan["rp"], plan["ci"], self._np(vals), self._np(A),
+                                         self._np(B), self._np(G), plan["n"])
+        dA += torch.from_numpy(ga).to(dA.dtype)
+        dB += torch.from_numpy(gb).to(dB.dtype)
+        ds.copy_(torch.from_numpy(gs).to(ds.dtype))
+
+    def close(self, plan):
+        pass
+
+
+def rank_main(rank, world, port, out, seed, r, use_gpu, vals_none):
+    import torch.distributed as dist
+    from paper_2203_07673_gb300 import dist15d
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        S, vals, A, B, G = problem(seed, r=r)
+        rb = dist15d.row_bounds_by_nnz(S.row_ptr, world)
+        cb = dist15d.col_bounds_uniform(S.n, world)
+        r0, r1 = int(rb[rank]), int(rb[rank + 1])
+        c0, c1 = int(cb[rank]), int(cb[rank + 1])
+        p0, p1 = int(S.row_ptr[r0]), int(S.row_ptr[r1])
+        dev = torch.device("cuda", 0) if use_gpu else torch.device("cpu")
+        rp = torch.from_numpy((S.row_ptr[r0:r1 + 1].astype(np.int64) - p0).astype(np.int32)).to(dev)
+        ci = torch.from_numpy(S.col_idx[p0:p1].copy()).to(dev)
+        vk = None if vals_none else torch.from_numpy(vals[p0:p1].copy()).to(dev)
+        Ak = torch.from_numpy(A[r0:r1].copy()).to(dev)
+        Bk = torch.from_numpy(B[c0:c1].copy()).to(dev)
+        Gk = torch.from_numpy(G[r0:r1].copy()).to(dev)
+        ops = None if use_gpu else OracleOps()
+        d = dist15d.FusedMM15D(rp, ci, S.n, r, torch.float32, ops=ops)
+        assert [d.block_of_phase(t) for t in range(world)] == [(rank + t) % world
+                                                               for t in range(world)]
+        res = dict(out=d.fusedmm(vk, Ak, Bk), out_t=d.fusedmm_t(vk, Ak, Bk))
+        res["dA"], res["dB"], res["ds"] = d.fusedmm_bwd(vk, Ak, Bk, Gk)
+        if use_gpu:
+            torch.cuda.synchronize()
+        out[rank] = {k: v.cpu().numpy() for k, v in res.items()}
+        out[f"bounds{rank}"] = (r0, r1, c0, c1, p0, p1)
+        d.close()
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()

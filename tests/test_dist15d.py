@@ -1,0 +1,112 @@
+"""1.5D dense-shifting FusedMM with local kernel fusion (Sec. V, Algorithm 1,
+c = 1) on CPU: 2 and 3 gloo ranks, local calls evaluated by the oracle, the
+assembled FusedMMA, FusedMMB, dA, dB and ds against the oracle on the whole
+matrix; and the index arithmetic of the partition."""
+import os
+import socket
+import sys
+
+import numpy as np
+import pytest
+import torch
+import torch.multiprocessing as mp
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+from paper_2203_07673_gb300 import dist15d  # noqa: E402
+from paper_2203_07673_gb300 import workloads as wl  # noqa: E402
+
+
+def free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def run_ranks(world, seed, r, use_gpu, vals_none=False):
+    import dist15d_ranks
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
+    port = free_port()
+    procs = [ctx.Process(target=dist15d_ranks.rank_main,
+                         args=(k, world, port, out, seed, r, use_gpu, vals_none))
+             for k in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=300)
+    assert all(p.exitcode == 0 for p in procs), [p.exitcode for p in procs]
+    return dict(out)
+
+
+def assemble(res, world, S, r):
+    out = np.zeros((S.m, r)); out_t = np.zeros((S.n, r))
+    dA = np.zeros((S.m, r)); dB = np.zeros((S.n, r)); ds = np.zeros(S.nnz)
+    for k in range(world):
+        r0, r1, c0, c1, p0, p1 = res[f"bounds{k}"]
+        out[r0:r1] = res[k]["out"]; dA[r0:r1] = res[k]["dA"]; ds[p0:p1] = res[k]["ds"]
+        out_t[c0:c1] = res[k]["out_t"]; dB[c0:c1] = res[k]["dB"]
+    return out, out_t, dA, dB, ds
+
+
+def expected(S, vals, A, B, G):
+    rp, ci, n = S.row_ptr, S.col_idx, S.n
+    A64, B64 = A.astype(np.float64), B.astype(np.float64)
+    ga, gb, gs = oracle.fusedmm_grad(rp, ci, vals, A64, B64, G.astype(np.float64), n)
+    return (oracle.fusedmm(rp, ci, vals, A64, B64, n), oracle.fusedmm_t(rp, ci, vals, A64, B64, n),
+            ga, gb, gs)
+
+
+def rel(x, y):
+    return np.linalg.norm(x - y) / max(np.linalg.norm(y), 1e-300)
+
+
+def test_row_bounds_balance_nonzeros_and_cover_every_row():
+    rng = np.random.default_rng(0)
+    S = wl.random_csr(1000, 300, rng, mean_deg=8, hubs=((5, 900),))
+    for parts in (1, 2, 3, 7):
+        b = dist15d.row_bounds_by_nnz(S.row_ptr, parts)
+        assert b[0] == 0 and b[-1] == S.m and np.all(np.diff(b) >= 0)
+        counts = np.diff(S.row_ptr.astype(np.int64)[b])
+        assert counts.sum() == S.nnz
+        # a block misses its share by less than one row's nonzeros
+        assert np.all(np.abs(counts - S.nnz / parts) <= S.degrees().max() + 1)
+    cb = dist15d.col_bounds_uniform(250, 3)
+    assert list(cb) == [0, 83, 166, 250]
+
+
+def test_split_by_column_blocks_is_a_partition():
+    rng = np.random.default_rng(1)
+    S = wl.random_csr(200, 97, rng, mean_deg=6, dup_frac=0.1, unsorted=True)
+    rp = torch.from_numpy(S.row_ptr); ci = torch.from_numpy(S.col_idx)
+    cb = dist15d.col_bounds_uniform(S.n, 4)
+    blocks = dist15d.split_by_column_blocks(rp, ci, cb)
+    seen = np.concatenate([b[2].numpy() for b in blocks])
+    assert np.array_equal(np.sort(seen), np.arange(S.nnz))
+    row_of = np.repeat(np.arange(S.m), S.degrees())
+    for l, (brp, bci, sel) in enumerate(blocks):
+        sel = sel.numpy()
+        assert np.all((S.col_idx[sel] >= cb[l]) & (S.col_idx[sel] < cb[l + 1]))
+        assert np.array_equal(bci.numpy(), S.col_idx[sel] - cb[l])
+        # rows of the block's CSR are the rows the selected nonzeros sit in,
+        # in the input order within each row
+        brow = np.repeat(np.arange(S.m), np.diff(brp.numpy().astype(np.int64)))
+        assert np.array_equal(brow, row_of[sel])
+        assert np.all(np.diff(sel)[np.diff(brow) == 0] > 0)
+
+
+@pytest.mark.parametrize("world", [2, 3])
+@pytest.mark.parametrize("vals_none", [False, True])
+def test_ring_schedule_matches_the_whole_matrix(world, vals_none):
+    import dist15d_ranks
+    seed, r = 11 + world, 8
+    S, vals, A, B, G = dist15d_ranks.problem(seed, r=r)
+    res = run_ranks(world, seed, r, use_gpu=False, vals_none=vals_none)
+    got = assemble(res, world, S, r)
+    want = expected(S, None if vals_none else vals, A, B, G)
+    for name, x, y in zip(("out", "out_t", "dA", "dB", "ds"), got, want):
+        assert rel(x, y) <= 1e-6, name

@@ -1,0 +1,27 @@
+"""1.5D dense-shifting FusedMM with local kernel fusion (Sec. V, Algorithm 1,
+c = 1) with the library's kernels: two gloo ranks on the one GPU (the
+shifts staged through host memory; no kernel waits on another rank), the
+assembled FusedMMA, FusedMMB, dA, dB and ds against the FP64 oracle on the
+whole matrix, within the float32 parity bar.  Every local call is an
+accumulating one (fmm_fusedmm_acc, fmm_fusedmm_t_acc, fmm_fusedmm_bwd_acc)
+over one column block of the rank's rows."""
+import numpy as np
+import pytest
+
+from test_dist15d import assemble, expected, rel, run_ranks
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("r", [32, 24])
+@pytest.mark.parametrize("vals_none", [False, True])
+def test_two_ranks_on_one_gpu_match_the_whole_matrix(r, vals_none):
+    import dist15d_ranks
+    seed = 21 + r
+    S, vals, A, B, G = dist15d_ranks.problem(seed, r=r)
+    res = run_ranks(2, seed, r, use_gpu=True, vals_none=vals_none)
+    got = assemble(res, 2, S, r)
+    want = expected(S, None if vals_none else vals, A, B, G)
+    for name, x, y in zip(("out", "out_t", "dA", "dB", "ds"), got, want):
+        assert np.all(np.isfinite(x)), name
+        assert rel(x, y) <= 1e-5, name

@@ -405,3 +405,39 @@ def test_rows_without_nonzeros_are_zeroed():
             h = go.cpu().numpy()
             assert np.all(h[deg == 0] == 0.0) and np.all(np.isfinite(h))
         plan.close()
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16], ids=["f32", "bf16"])
+@pytest.mark.parametrize("variant", [0, 212, 1042, 32212, 44042])
+@pytest.mark.parametrize("r", [32, 128, 24])
+def test_accumulating_calls_add_to_the_output(r, variant, dtype):
+    """fmm_fusedmm_acc / _t_acc / _bwd_acc add the pass to what the outputs
+    hold (split rows and columns included): acc(X0) equals X0 + the plain
+    call, bit for bit where X0 = 0, within rounding otherwise."""
+    from paper_2203_07673_gb300 import fmm
+    S, _ = pattern("hubs", 5)
+    rng = np.random.default_rng(9)
+    A = rng.standard_normal((S.m, r)).astype(np.float32)
+    B = rng.standard_normal((S.n, r)).astype(np.float32)
+    vals = rng.uniform(0, 1, S.nnz).astype(np.float32)
+    rp, ci, vt, At, Bt = upload(S, vals, A, B, dtype)
+    plan = fmm.Plan(rp, ci, S.n, r, dtype, split_nnz=64, variant=variant)
+    G = torch.randn(S.m, r, device="cuda")
+    ref = fmm.fusedmm(plan, vt, At, Bt)
+    ref_t = fmm.fusedmm_t(plan, vt, At, Bt)
+    rdA, rdB, rds = fmm.fusedmm_bwd(plan, vt, At, Bt, G)
+    z = lambda *s: torch.zeros(s, device="cuda")  # noqa: E731
+    assert torch.equal(fmm.fusedmm_acc(plan, vt, At, Bt, z(S.m, r)), ref)
+    assert torch.equal(fmm.fusedmm_t_acc(plan, vt, At, Bt, z(S.n, r)), ref_t)
+    dA, dB, ds = fmm.fusedmm_bwd_acc(plan, vt, At, Bt, G, z(S.m, r), z(S.n, r), z(S.nnz))
+    assert torch.equal(dA, rdA) and torch.equal(dB, rdB) and torch.equal(ds, rds)
+    X0, Y0 = torch.randn(S.m, r, device="cuda"), torch.randn(S.n, r, device="cuda")
+    got = fmm.fusedmm_acc(plan, vt, At, Bt, X0.clone())
+    got_t = fmm.fusedmm_t_acc(plan, vt, At, Bt, Y0.clone())
+    # the vector passes add X0 to the finished row (one rounding, as X0 +
+    # ref); the generic pass starts its sum from X0 (another order), so the
+    # difference is rounding-sized, far below a missing X0 or term
+    for g, w in ((got, X0 + ref), (got_t, Y0 + ref_t)):
+        err = (g - w).abs().max().item()
+        assert err <= 1e-5 * max(1.0, w.abs().max().item()), err
+    plan.close()
