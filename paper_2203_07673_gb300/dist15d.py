@@ -117,8 +117,9 @@ class FusedMM15D:
     def __init__(self, row_ptr, col_idx, n, r, dtype=torch.float32, group=None, col_bounds=None,
                  ops=None):
         self.group = group
-        self.p = dist.get_world_size(group)
-        self.k = dist.get_rank(group)
+        # without a process group: one rank (p = 1, no shifts)
+        self.p = dist.get_world_size(group) if dist.is_initialized() else 1
+        self.k = dist.get_rank(group) if dist.is_initialized() else 0
         self.n, self.r, self.dtype = int(n), int(r), dtype
         self.col_bounds = (col_bounds_uniform(self.n, self.p) if col_bounds is None
                            else np.asarray(col_bounds, dtype=np.int64))

@@ -110,3 +110,17 @@ def test_ring_schedule_matches_the_whole_matrix(world, vals_none):
     want = expected(S, None if vals_none else vals, A, B, G)
     for name, x, y in zip(("out", "out_t", "dA", "dB", "ds"), got, want):
         assert rel(x, y) <= 1e-6, name
+
+
+def test_one_rank_without_a_process_group():
+    """p = 1 when no process group exists: one phase, no shift."""
+    import dist15d_ranks
+    S, vals, A, B, G = dist15d_ranks.problem(3, r=8)
+    d = dist15d.FusedMM15D(torch.from_numpy(S.row_ptr), torch.from_numpy(S.col_idx), S.n, 8,
+                           torch.float32, ops=dist15d_ranks.OracleOps())
+    assert d.p == 1 and d.k == 0
+    Vt, At, Bt, Gt = (torch.from_numpy(x) for x in (vals, A, B, G))
+    got = (d.fusedmm(Vt, At, Bt), d.fusedmm_t(Vt, At, Bt)) + d.fusedmm_bwd(Vt, At, Bt, Gt)
+    want = expected(S, vals, A, B, G)
+    for x, y in zip(got, want):
+        assert rel(x.double().numpy(), y) <= 1e-6
