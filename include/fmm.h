@@ -277,6 +277,15 @@ int fmm_fusedmm_t_acc(const fmm_plan *plan, const float *vals, const void *A, co
                       float *out_n, fmm_stream stream);
 int fmm_fusedmm_bwd_acc(const fmm_plan *plan, const float *vals, const void *A, const void *B,
                         const float *G, float *dA, float *dB, float *ds, fmm_stream stream);
+/* v_out += SDDMM (the partial dot products of one column slice of A and B,
+ * summed over the slices by the 1.5D sparse-shifting algorithm, Sec. V);
+ * out_m += SpMMA;  out_n += SpMMB. */
+int fmm_sddmm_acc(const fmm_plan *plan, const float *vals, const void *A, const void *B,
+                  float *v_out, fmm_stream stream);
+int fmm_spmm_acc(const fmm_plan *plan, const float *v, const void *B, float *out_m,
+                 fmm_stream stream);
+int fmm_spmm_t_acc(const fmm_plan *plan, const float *v, const void *A, float *out_n,
+                   fmm_stream stream);
 
 /*
  * Kernel variant of a plan's row passes (the codes of

@@ -329,28 +329,30 @@ int fmm_plan_get_info(const fmm_plan *p, fmm_plan_info *info)
     return FMM_OK;
 }
 
-int fmm_sddmm(const fmm_plan *p, const float *vals, const void *A, const void *B, float *v_out,
-              fmm_stream stream)
+static int sddmm_(const fmm_plan *p, const float *vals, const void *A, const void *B,
+                  float *v_out, fmm_stream stream, bool acc)
 {
     CHECK(check_plan(p));
     CHECK(need(A, p->m, "A"));
     CHECK(need(B, p->n, "B"));
     CHECK(need(v_out, p->nnz, "v_out"));
     return run_pass(p, p->rows, M_SDDMM, vals, A, B, nullptr, nullptr, v_out,
-                    (cudaStream_t)stream);
+                    (cudaStream_t)stream, acc);
 }
 
-int fmm_spmm(const fmm_plan *p, const float *v, const void *B, float *out_m, fmm_stream stream)
+static int spmm_(const fmm_plan *p, const float *v, const void *B, float *out_m,
+                 fmm_stream stream, bool acc)
 {
     CHECK(check_plan(p));
     CHECK(need(v, p->nnz, "v"));
     CHECK(need(B, p->n, "B"));
     CHECK(need(out_m, p->m, "out_m"));
     return run_pass(p, p->rows, M_SPMM, v, nullptr, B, nullptr, out_m, nullptr,
-                    (cudaStream_t)stream);
+                    (cudaStream_t)stream, acc);
 }
 
-int fmm_spmm_t(const fmm_plan *p, const float *v, const void *A, float *out_n, fmm_stream stream)
+static int spmm_t_(const fmm_plan *p, const float *v, const void *A, float *out_n,
+                   fmm_stream stream, bool acc)
 {
     CHECK(check_plan(p));
     CHECK(need_t(p));
@@ -358,7 +360,41 @@ int fmm_spmm_t(const fmm_plan *p, const float *v, const void *A, float *out_n, f
     CHECK(need(A, p->m, "A"));
     CHECK(need(out_n, p->n, "out_n"));
     return run_pass(p, p->cols, M_SPMM, v, nullptr, A, nullptr, out_n, nullptr,
-                    (cudaStream_t)stream);
+                    (cudaStream_t)stream, acc);
+}
+
+int fmm_sddmm(const fmm_plan *p, const float *vals, const void *A, const void *B, float *v_out,
+              fmm_stream stream)
+{
+    return sddmm_(p, vals, A, B, v_out, stream, false);
+}
+
+int fmm_spmm(const fmm_plan *p, const float *v, const void *B, float *out_m, fmm_stream stream)
+{
+    return spmm_(p, v, B, out_m, stream, false);
+}
+
+int fmm_spmm_t(const fmm_plan *p, const float *v, const void *A, float *out_n, fmm_stream stream)
+{
+    return spmm_t_(p, v, A, out_n, stream, false);
+}
+
+int fmm_sddmm_acc(const fmm_plan *p, const float *vals, const void *A, const void *B,
+                  float *v_out, fmm_stream stream)
+{
+    return sddmm_(p, vals, A, B, v_out, stream, true);
+}
+
+int fmm_spmm_acc(const fmm_plan *p, const float *v, const void *B, float *out_m,
+                 fmm_stream stream)
+{
+    return spmm_(p, v, B, out_m, stream, true);
+}
+
+int fmm_spmm_t_acc(const fmm_plan *p, const float *v, const void *A, float *out_n,
+                   fmm_stream stream)
+{
+    return spmm_t_(p, v, A, out_n, stream, true);
 }
 
 static int fusedmm_a(const fmm_plan *p, const float *vals, const void *A, const void *B,

@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(256, MB) bulk_pass_kernel(const PassArgs a)
                     for (int t = 0; t < E2; ++t) acc2[t] = ffma2(c2, y2[t], acc2[t]);
                 } else {   // M_SDDMM
                     if (use && sidx >= 0 && lig == 0)
-                        a.nzout[sidx] = sv * dd;
+                        nz_store<MODE>(a, sidx, sv * dd);
                 }
             }
             // every lane has read slot d (its values are in registers and

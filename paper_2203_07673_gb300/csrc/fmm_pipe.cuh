@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(256, MB) pipe_pass_kernel(const PassArgs a)
 #pragma unroll
             for (int e = 0; e < K; ++e)
                 if (ic[e] >= 0)
-                    a.nzout[ic[e]] = held[e];
+                    nz_store<MODE>(a, ic[e], held[e]);
         }
         // the next block becomes current; fetch the one after it
 #pragma unroll

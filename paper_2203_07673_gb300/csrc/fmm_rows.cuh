@@ -123,6 +123,18 @@ __device__ __forceinline__ float pick(const float (&x)[K], int e)
     return r;
 }
 
+// A per-nonzero output: SDDMM values are added to what v holds in the
+// accumulating calls (the partial dot products of the sparse-shifting
+// algorithm); ds is always overwritten.
+template <int MODE>
+__device__ __forceinline__ void nz_store(const PassArgs &a, int slot, float v)
+{
+    if (MODE == M_SDDMM && a.accumulate)
+        a.nzout[slot] += v;
+    else
+        a.nzout[slot] = v;
+}
+
 // Work item of group `gid`: chunks of split rows first, then light rows in
 // plan order.  slot >= 0 marks a chunk (its partial row goes to partials).
 __device__ __forceinline__ void pass_item(const PassArgs &a, long long gid, int &row,
@@ -355,7 +367,7 @@ __device__ __forceinline__ void team_pass_body(const PassArgs &a, long long gid,
                         if ((lane & (TEAM - 1)) == first + u)
                             held = sv[u] * d[u];
                     } else if (lig == (u % G)) {
-                        a.nzout[sidx[u]] = sv[u] * d[u];
+                        nz_store<MODE>(a, sidx[u], sv[u] * d[u]);
                     }
                 } else if constexpr (MODE == M_BWD_ROW) {
                     if constexpr (HOLD) {
@@ -415,7 +427,7 @@ __device__ __forceinline__ void team_pass_body(const PassArgs &a, long long gid,
             // the block's per-nonzero outputs, one store per lane
             if constexpr (HOLD)
                 if (q < end && a.nzout)
-                    a.nzout[mysi] = held;
+                    nz_store<MODE>(a, mysi, held);
         }
     } else {
         const int iters = (end - beg + PER - 1) / PER;
@@ -546,7 +558,7 @@ __global__ void __launch_bounds__(256) row_pass_generic(const PassArgs a)
         }
         if constexpr (MODE == M_SDDMM) {
             if (lane == 0)
-                a.nzout[sidx] = sv * d;
+                nz_store<MODE>(a, sidx, sv * d);
         } else if constexpr (MODE == M_BWD_ROW) {
             if (lane == 0 && a.nzout)
                 a.nzout[sidx] = d * w;

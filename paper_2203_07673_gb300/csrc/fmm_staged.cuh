@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(256) staged_pass_kernel(const PassArgs a)
                     for (int t = 0; t < E; ++t) acc[t] = fmaf(c, y[t], acc[t]);
                 } else {   // M_SDDMM
                     if (lig == (k % G))
-                        a.nzout[si] = s * d[0];
+                        nz_store<MODE>(a, si, s * d[0]);
                 }
             }
         }

@@ -1,4 +1,6 @@
-"""1.5D dense-shifting FusedMM with local kernel fusion (Sec. V, Algorithm 1, c = 1).
+"""Distributed FusedMM (Sec. V), replication factor c = 1: the 1.5D
+dense-shifting algorithm with local kernel fusion (Algorithm 1,
+FusedMM15D) and the 1.5D sparse-shifting algorithm (SparseShift15D).
 
 p ranks in one ring (a p x 1 grid: replication factor c = 1).  Rank k owns
   * a block of rows of S (R_k, balanced by nonzeros), the same rows of A and of
@@ -98,6 +100,15 @@ class LibraryOps:
 
     def fusedmm_bwd_acc(self, plan, vals, A, B, G, dA, dB, ds):
         self.fmm.fusedmm_bwd_acc(plan, vals, A, B, G, dA, dB, ds)
+
+    def sddmm_acc(self, plan, vals, A, B, v):
+        self.fmm.sddmm_acc(plan, vals, A, B, v)
+
+    def spmm(self, plan, v, B, out):
+        self.fmm.spmm(plan, v, B, out=out)
+
+    def spmm_t_acc(self, plan, v, A, out):
+        self.fmm.spmm_t_acc(plan, v, A, out)
 
     def close(self, plan):
         plan.close()
@@ -244,3 +255,110 @@ class FusedMM15D:
             self._wait(pend + self._shift(dBs[cur], dBs[1 - cur]))
             cur = 1 - cur
         return dA, dBs[cur][:self._width(self.k)].clone(), ds
+
+
+def slice_bounds(r: int, parts: int) -> np.ndarray:
+    """Column slices of the dense width r (parts + 1 boundaries)."""
+    return np.array([(k * r) // parts for k in range(parts + 1)], dtype=np.int64)
+
+
+class SparseShift15D:
+    """FusedMMA and FusedMMB by the 1.5D sparse-shifting, dense-replicating
+    algorithm (Sec. V, c = 1): the dense matrices are divided by column
+    slices of r, the sparse matrix by block rows, and the block rows circulate.
+
+    Local kernel fusion is impossible in this layout (a rank holds only a
+    slice of every row of A and B, so no rank can finish a dot product before
+    the aggregation, Sec. IV-B), so FusedMM runs as SDDMM then SpMM: round 1
+    passes each block row's values around the ring, every rank adding its
+    slice's partial dot products (fmm_sddmm_acc); after p phases and p shifts
+    each block is back at its owner with its SDDMM values complete.  Round 2
+    passes the completed blocks around again, every rank applying each block
+    to its column slice (fmm_spmm for FusedMMA rows; fmm_spmm_t_acc, summed
+    over the blocks, for FusedMMB).  The patterns are laid out on every rank
+    once (one plan per block row, at the rank's slice width), so only the
+    values travel: nnz/p floats per shift.
+
+    Every rank passes the whole pattern (row_ptr, col_idx: int32 on its
+    device), the values of all nonzeros (or None), its column slices A_k
+    (m x r_k) and B_k (n x r_k), and gets its slices of the outputs."""
+
+    def __init__(self, row_ptr, col_idx, n, r, dtype=torch.float32, group=None, ops=None,
+                 row_bounds=None):
+        self.group = group
+        self.p = dist.get_world_size(group) if dist.is_initialized() else 1
+        self.k = dist.get_rank(group) if dist.is_initialized() else 0
+        self.n, self.r, self.dtype = int(n), int(r), dtype
+        self.m = row_ptr.numel() - 1
+        self.ops = ops if ops is not None else LibraryOps()
+        rp_h = row_ptr.cpu().numpy()
+        self.row_bounds = (row_bounds_by_nnz(rp_h, self.p) if row_bounds is None
+                           else np.asarray(row_bounds, dtype=np.int64))
+        self.slices = slice_bounds(self.r, self.p)
+        self.width = int(self.slices[self.k + 1] - self.slices[self.k])
+        self.nnz_bounds = rp_h.astype(np.int64)[self.row_bounds]
+        self.plans = []
+        for b in range(self.p):
+            r0, r1 = int(self.row_bounds[b]), int(self.row_bounds[b + 1])
+            p0, p1 = int(self.nnz_bounds[b]), int(self.nnz_bounds[b + 1])
+            rp = (row_ptr[r0:r1 + 1].long() - p0).to(torch.int32)
+            self.plans.append(self.ops.plan(rp, col_idx[p0:p1], self.n, self.width, dtype))
+        self.maxnz = int(np.diff(self.nnz_bounds).max()) if self.p else 0
+        self._ring = FusedMM15D.__new__(FusedMM15D)   # borrows its shift helpers
+        self._ring.group, self._ring.p, self._ring.k = group, self.p, self.k
+
+    def close(self):
+        for pl in self.plans:
+            self.ops.close(pl)
+        self.plans = []
+
+    def block_of_phase(self, t: int) -> int:
+        return (self.k + t) % self.p
+
+    def _rows(self, b):
+        return int(self.row_bounds[b]), int(self.row_bounds[b + 1])
+
+    def _nz(self, b):
+        return int(self.nnz_bounds[b]), int(self.nnz_bounds[b + 1])
+
+    def _sddmm_round(self, vals, A_k, B_k):
+        """Round 1: every block row's SDDMM values, summed over the slices;
+        returns (this rank's block values, padded buffer pair, current)."""
+        dev = A_k.device
+        bufs = [torch.zeros(self.maxnz, dtype=torch.float32, device=dev),
+                torch.empty(self.maxnz, dtype=torch.float32, device=dev)]
+        cur = 0
+        for t in range(self.p):
+            b = self.block_of_phase(t)
+            (r0, r1), (p0, p1) = self._rows(b), self._nz(b)
+            v = None if vals is None else vals[p0:p1]
+            self.ops.sddmm_acc(self.plans[b], v, A_k[r0:r1], B_k, bufs[cur][:p1 - p0])
+            self._ring._wait(self._ring._shift(bufs[cur], bufs[1 - cur]))
+            cur = 1 - cur
+        return bufs, cur
+
+    def fusedmm(self, vals, A_k, B_k):
+        """This rank's column slice of FusedMMA (m x r_k)."""
+        bufs, cur = self._sddmm_round(vals, A_k, B_k)
+        out = torch.empty((self.m, self.width), dtype=torch.float32, device=A_k.device)
+        for t in range(self.p):
+            b = self.block_of_phase(t)
+            (r0, r1), (p0, p1) = self._rows(b), self._nz(b)
+            pend = self._ring._shift(bufs[cur], bufs[1 - cur]) if t + 1 < self.p else []
+            self.ops.spmm(self.plans[b], bufs[cur][:p1 - p0], B_k, out[r0:r1])
+            self._ring._wait(pend)
+            cur = 1 - cur
+        return out
+
+    def fusedmm_t(self, vals, A_k, B_k):
+        """This rank's column slice of FusedMMB (n x r_k)."""
+        bufs, cur = self._sddmm_round(vals, A_k, B_k)
+        out = torch.zeros((self.n, self.width), dtype=torch.float32, device=A_k.device)
+        for t in range(self.p):
+            b = self.block_of_phase(t)
+            (r0, r1), (p0, p1) = self._rows(b), self._nz(b)
+            pend = self._ring._shift(bufs[cur], bufs[1 - cur]) if t + 1 < self.p else []
+            self.ops.spmm_t_acc(self.plans[b], bufs[cur][:p1 - p0], A_k[r0:r1], out)
+            self._ring._wait(pend)
+            cur = 1 - cur
+        return out

@@ -39,6 +39,9 @@ _SIGNATURES = {
     "fmm_fusedmm_bwd": ([_P, _P, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "fmm_fusedmm_t_bwd": ([_P, _P, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "fmm_fusedmm_acc": ([_P, _P, _P, _P, _P, _P], ctypes.c_int),
+    "fmm_sddmm_acc": ([_P, _P, _P, _P, _P, _P], ctypes.c_int),
+    "fmm_spmm_acc": ([_P, _P, _P, _P, _P], ctypes.c_int),
+    "fmm_spmm_t_acc": ([_P, _P, _P, _P, _P], ctypes.c_int),
     "fmm_fusedmm_t_acc": ([_P, _P, _P, _P, _P, _P], ctypes.c_int),
     "fmm_fusedmm_bwd_acc": ([_P, _P, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "fmm_fusedmm_noalloc": ([_P, _I32, _I32, _P, _P, _P, _P, _P], ctypes.c_int),
@@ -299,6 +302,33 @@ def fusedmm_bwd(plan: Plan, vals, A, B, G, need=(True, True, True), stream=None)
                                plan._f32(ds, (plan.nnz,), "ds"), _stream(stream))
     _check(rc, "fmm_fusedmm_bwd")
     return dA, dB, ds
+
+
+def sddmm_acc(plan: Plan, vals, A, B, v, stream=None):
+    """fmm_sddmm_acc: v += SDDMM (v float32, nnz, valid values)."""
+    rc = lib().fmm_sddmm_acc(plan.handle, plan._f32(vals, (plan.nnz,), "vals"),
+                             plan._dense(A, plan.m, "A"), plan._dense(B, plan.n, "B"),
+                             plan._f32(v, (plan.nnz,), "v"), _stream(stream))
+    _check(rc, "fmm_sddmm_acc")
+    return v
+
+
+def spmm_acc(plan: Plan, v, B, out, stream=None):
+    """fmm_spmm_acc: out += SpMMA(v, B) (out float32, m x r)."""
+    rc = lib().fmm_spmm_acc(plan.handle, plan._f32(v, (plan.nnz,), "v"),
+                            plan._dense(B, plan.n, "B"), plan._f32(out, (plan.m, plan.r), "out"),
+                            _stream(stream))
+    _check(rc, "fmm_spmm_acc")
+    return out
+
+
+def spmm_t_acc(plan: Plan, v, A, out, stream=None):
+    """fmm_spmm_t_acc: out += SpMMB(v, A) (out float32, n x r)."""
+    rc = lib().fmm_spmm_t_acc(plan.handle, plan._f32(v, (plan.nnz,), "v"),
+                              plan._dense(A, plan.m, "A"), plan._f32(out, (plan.n, plan.r), "out"),
+                              _stream(stream))
+    _check(rc, "fmm_spmm_t_acc")
+    return out
 
 
 def fusedmm_acc(plan: Plan, vals, A, B, out, stream=None):

@@ -61,6 +61,19 @@ class OracleOps:
         dB += torch.from_numpy(gb).to(dB.dtype)
         ds.copy_(torch.from_numpy(gs).to(ds.dtype))
 
+    def sddmm_acc(self, plan, vals, A, B, v):
+        res = self.o.sddmm(plan["rp"], plan["ci"], self._np(vals), self._np(A), self._np(B),
+                           plan["n"])
+        v += torch.from_numpy(res).to(v.dtype)
+
+    def spmm(self, plan, v, B, out):
+        res = self.o.spmm(plan["rp"], plan["ci"], self._np(v), self._np(B), plan["n"])
+        out.copy_(torch.from_numpy(res).to(out.dtype))
+
+    def spmm_t_acc(self, plan, v, A, out):
+        res = self.o.spmm_t(plan["rp"], plan["ci"], self._np(v), self._np(A), plan["n"])
+        out += torch.from_numpy(res).to(out.dtype)
+
     def close(self, plan):
         pass
 
@@ -94,6 +107,36 @@ def rank_main(rank, world, port, out, seed, r, use_gpu, vals_none):
             torch.cuda.synchronize()
         out[rank] = {k: v.cpu().numpy() for k, v in res.items()}
         out[f"bounds{rank}"] = (r0, r1, c0, c1, p0, p1)
+        d.close()
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def sparse_rank_main(rank, world, port, out, seed, r, use_gpu, vals_none):
+    """The sparse-shifting algorithm: every rank holds the whole pattern and
+    values and its column slices of A and B; returns its output slices."""
+    import torch.distributed as dist
+    from paper_2203_07673_gb300 import dist15d
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        S, vals, A, B, G = problem(seed, r=r)
+        sl = dist15d.slice_bounds(r, world)
+        j0, j1 = int(sl[rank]), int(sl[rank + 1])
+        dev = torch.device("cuda", 0) if use_gpu else torch.device("cpu")
+        rp = torch.from_numpy(S.row_ptr.copy()).to(dev)
+        ci = torch.from_numpy(S.col_idx.copy()).to(dev)
+        vt = None if vals_none else torch.from_numpy(vals).to(dev)
+        Ak = torch.from_numpy(np.ascontiguousarray(A[:, j0:j1])).to(dev)
+        Bk = torch.from_numpy(np.ascontiguousarray(B[:, j0:j1])).to(dev)
+        ops = None if use_gpu else OracleOps()
+        d = dist15d.SparseShift15D(rp, ci, S.n, r, torch.float32, ops=ops)
+        res = dict(out=d.fusedmm(vt, Ak, Bk), out_t=d.fusedmm_t(vt, Ak, Bk))
+        if use_gpu:
+            torch.cuda.synchronize()
+        out[rank] = {k: v.cpu().numpy() for k, v in res.items()}
+        out[f"slice{rank}"] = (j0, j1)
         d.close()
         dist.barrier()
     finally:

@@ -1,7 +1,8 @@
-"""1.5D dense-shifting FusedMM with local kernel fusion (Sec. V, Algorithm 1,
-c = 1) on CPU: 2 and 3 gloo ranks, local calls evaluated by the oracle, the
-assembled FusedMMA, FusedMMB, dA, dB and ds against the oracle on the whole
-matrix; and the index arithmetic of the partition."""
+"""Distributed FusedMM (Sec. V, c = 1) on CPU: the 1.5D dense-shifting
+algorithm with local kernel fusion (Algorithm 1) and the 1.5D sparse-shifting
+algorithm, 2 and 3 gloo ranks, local calls evaluated by the oracle, the
+assembled outputs against the oracle on the whole matrix; and the index
+arithmetic of the partitions."""
 import os
 import socket
 import sys
@@ -26,13 +27,13 @@ def free_port():
         return s.getsockname()[1]
 
 
-def run_ranks(world, seed, r, use_gpu, vals_none=False):
+def run_ranks(world, seed, r, use_gpu, vals_none=False, body="rank_main"):
     import dist15d_ranks
     ctx = mp.get_context("spawn")
     mgr = ctx.Manager()
     out = mgr.dict()
     port = free_port()
-    procs = [ctx.Process(target=dist15d_ranks.rank_main,
+    procs = [ctx.Process(target=getattr(dist15d_ranks, body),
                          args=(k, world, port, out, seed, r, use_gpu, vals_none))
              for k in range(world)]
     for p in procs:
@@ -124,3 +125,30 @@ def test_one_rank_without_a_process_group():
     want = expected(S, vals, A, B, G)
     for x, y in zip(got, want):
         assert rel(x.double().numpy(), y) <= 1e-6
+
+
+def assemble_slices(res, world, S, r):
+    out = np.zeros((S.m, r)); out_t = np.zeros((S.n, r))
+    for k in range(world):
+        j0, j1 = res[f"slice{k}"]
+        out[:, j0:j1] = res[k]["out"]; out_t[:, j0:j1] = res[k]["out_t"]
+    return out, out_t
+
+
+@pytest.mark.parametrize("world", [2, 3])
+@pytest.mark.parametrize("vals_none", [False, True])
+def test_sparse_shifting_matches_the_whole_matrix(world, vals_none):
+    import dist15d_ranks
+    seed, r = 31 + world, 9
+    S, vals, A, B, G = dist15d_ranks.problem(seed, r=r)
+    res = run_ranks(world, seed, r, use_gpu=False, vals_none=vals_none, body="sparse_rank_main")
+    got = assemble_slices(res, world, S, r)
+    want = expected(S, None if vals_none else vals, A, B, G)[:2]
+    for name, x, y in zip(("out", "out_t"), got, want):
+        assert rel(x, y) <= 1e-6, name
+
+
+def test_slice_bounds_cover_the_width():
+    for r, parts in ((9, 2), (64, 3), (5, 5)):
+        b = dist15d.slice_bounds(r, parts)
+        assert b[0] == 0 and b[-1] == r and np.all(np.diff(b) >= 1)

@@ -8,7 +8,7 @@ over one column block of the rank's rows."""
 import numpy as np
 import pytest
 
-from test_dist15d import assemble, expected, rel, run_ranks
+from test_dist15d import assemble, assemble_slices, expected, rel, run_ranks
 
 pytestmark = pytest.mark.gpu
 
@@ -23,5 +23,20 @@ def test_two_ranks_on_one_gpu_match_the_whole_matrix(r, vals_none):
     got = assemble(res, 2, S, r)
     want = expected(S, None if vals_none else vals, A, B, G)
     for name, x, y in zip(("out", "out_t", "dA", "dB", "ds"), got, want):
+        assert np.all(np.isfinite(x)), name
+        assert rel(x, y) <= 1e-5, name
+
+
+@pytest.mark.parametrize("r", [64, 24])
+def test_sparse_shifting_two_ranks_on_one_gpu(r):
+    """The sparse-shifting algorithm: column slices of 32 and 12 (r = 64, 24),
+    fmm_sddmm_acc / fmm_spmm / fmm_spmm_t_acc per block row and phase."""
+    import dist15d_ranks
+    seed = 41 + r
+    S, vals, A, B, G = dist15d_ranks.problem(seed, r=r)
+    res = run_ranks(2, seed, r, use_gpu=True, body="sparse_rank_main")
+    got = assemble_slices(res, 2, S, r)
+    want = expected(S, vals, A, B, G)[:2]
+    for name, x, y in zip(("out", "out_t"), got, want):
         assert np.all(np.isfinite(x)), name
         assert rel(x, y) <= 1e-5, name

@@ -411,9 +411,10 @@ def test_rows_without_nonzeros_are_zeroed():
 @pytest.mark.parametrize("variant", [0, 212, 1042, 32212, 44042])
 @pytest.mark.parametrize("r", [32, 128, 24])
 def test_accumulating_calls_add_to_the_output(r, variant, dtype):
-    """fmm_fusedmm_acc / _t_acc / _bwd_acc add the pass to what the outputs
-    hold (split rows and columns included): acc(X0) equals X0 + the plain
-    call, bit for bit where X0 = 0, within rounding otherwise."""
+    """fmm_fusedmm_acc / _t_acc / _bwd_acc and fmm_sddmm_acc / _spmm_acc /
+    _spmm_t_acc add the pass to what the outputs hold (split rows and
+    columns included): acc(X0) equals X0 + the plain call, bit for bit where
+    X0 = 0, within rounding otherwise."""
     from paper_2203_07673_gb300 import fmm
     S, _ = pattern("hubs", 5)
     rng = np.random.default_rng(9)
@@ -431,6 +432,13 @@ def test_accumulating_calls_add_to_the_output(r, variant, dtype):
     assert torch.equal(fmm.fusedmm_t_acc(plan, vt, At, Bt, z(S.n, r)), ref_t)
     dA, dB, ds = fmm.fusedmm_bwd_acc(plan, vt, At, Bt, G, z(S.m, r), z(S.n, r), z(S.nnz))
     assert torch.equal(dA, rdA) and torch.equal(dB, rdB) and torch.equal(ds, rds)
+    v = fmm.sddmm(plan, vt, At, Bt)
+    assert torch.equal(fmm.sddmm_acc(plan, vt, At, Bt, z(S.nnz)), v)
+    assert torch.equal(fmm.spmm_acc(plan, v, Bt, z(S.m, r)), fmm.spmm(plan, v, Bt))
+    assert torch.equal(fmm.spmm_t_acc(plan, v, At, z(S.n, r)), fmm.spmm_t(plan, v, At))
+    V0 = torch.randn(S.nnz, device="cuda")
+    err = (fmm.sddmm_acc(plan, vt, At, Bt, V0.clone()) - (V0 + v)).abs().max().item()
+    assert err <= 1e-5 * max(1.0, (V0 + v).abs().max().item()), err
     X0, Y0 = torch.randn(S.m, r, device="cuda"), torch.randn(S.n, r, device="cuda")
     got = fmm.fusedmm_acc(plan, vt, At, Bt, X0.clone())
     got_t = fmm.fusedmm_t_acc(plan, vt, At, Bt, Y0.clone())
