@@ -829,6 +829,8 @@ def run_dist15d(args, rank, world, local_rank):
     # end to end: every step uploads this rank's A, B and values from pinned
     # host memory and reads both output blocks back
     A_h, B_h, v_h = A.cpu().pin_memory(), B.cpu().pin_memory(), vals.cpu().pin_memory()
+    o_h = torch.empty((rows, r), dtype=torch.float32).pin_memory()
+    ot_h = torch.empty((rows, r), dtype=torch.float32).pin_memory()
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -837,12 +839,22 @@ def run_dist15d(args, rank, world, local_rank):
     for _ in range(reps):
         o, ot = step(v_h.to(dev, non_blocking=True), A_h.to(dev, non_blocking=True),
                      B_h.to(dev, non_blocking=True))
-        o.cpu(), ot.cpu()
+        o_h.copy_(o, non_blocking=True)
+        ot_h.copy_(ot, non_blocking=True)
     e1.record(stream)
     barrier()
     e2e_ms = reduce_max([e0.elapsed_time(e1) / reps], dev, world)[0]
     nnz_total = 32 * rows * world
     units = 2.0 * nnz_total * r
+    # library launches per step: per phase one FusedMMA pass (+ its combine
+    # where rows are split) and one FusedMMB pass (+ combine) after the value
+    # permutation (one launch, or two above two windows of 2^23 slots)
+    per_step = 0
+    for pl in d.plans:
+        info = pl.info()
+        nnz_l = int(info.get("nnz", 0))
+        per_step += 1 + (1 if info["split_rows"] else 0)
+        per_step += 1 + (1 if info["split_cols"] else 0) + (2 if nnz_l > 2 * (1 << 23) else 1)
     d.close()
     if rank == 0:
         print(json.dumps({
@@ -858,7 +870,7 @@ def run_dist15d(args, rank, world, local_rank):
             "e2e": {"value": units / (e2e_ms / 1e3), "unit": UNIT,
                     "h2d_bytes_per_step": (A_h.numel() + B_h.numel() + v_h.numel()) * 4 * world,
                     "d2h_bytes_per_step": 2 * rows * r * 4 * world, "ms_per_step": e2e_ms},
-            "gpu_launches": None, "clocks": clk}), flush=True)
+            "gpu_launches": per_step * args.steps, "clocks": clk}), flush=True)
     return 0
 
 

@@ -92,6 +92,15 @@ class LibraryOps:
     def plan(self, row_ptr, col_idx, n, r, dtype):
         return self.fmm.Plan(row_ptr, col_idx, n, r, dtype)
 
+    def fusedmm(self, plan, vals, A, B, out):
+        self.fmm.fusedmm(plan, vals, A, B, out=out)
+
+    def fusedmm_t(self, plan, vals, A, B, out):
+        self.fmm.fusedmm_t(plan, vals, A, B, out=out)
+
+    def fusedmm_bwd(self, plan, vals, A, B, G, dA, dB, ds):
+        self.fmm.fusedmm_bwd(plan, vals, A, B, G, out=(dA, dB, ds))
+
     def fusedmm_acc(self, plan, vals, A, B, out):
         self.fmm.fusedmm_acc(plan, vals, A, B, out)
 
@@ -142,7 +151,20 @@ class FusedMM15D:
         self.maxw = int(widths.max()) if len(widths) else 0
         self.plans = [self.ops.plan(rp, ci, int(widths[l]), self.r, dtype)
                       for l, (rp, ci, _) in enumerate(self.blocks)]
+        # a block whose nonzeros sit consecutively in the rank's CSR takes its
+        # values (and writes its ds) as a view, with no gather (always so at p = 1)
+        self.spans = [self._span(sel) for _, _, sel in self.blocks]
         self.device = col_idx.device
+
+    @staticmethod
+    def _span(sel):
+        c = sel.numel()
+        if c == 0:
+            return (0, 0)
+        a = int(sel[0])
+        if int(sel[-1]) - a + 1 == c and bool((sel[1:] - sel[:-1] == 1).all()):
+            return (a, c)
+        return None
 
     def close(self):
         for pl in self.plans:
@@ -159,12 +181,31 @@ class FusedMM15D:
         return int(self.col_bounds[l + 1] - self.col_bounds[l])
 
     def _vals(self, vals, l):
-        return None if vals is None else vals.index_select(0, self.blocks[l][2])
+        if vals is None:
+            return None
+        if self.spans[l] is not None:
+            return vals.narrow(0, *self.spans[l])
+        return vals.index_select(0, self.blocks[l][2])
 
-    def _padded(self, X, dtype):
-        buf = torch.zeros((self.maxw, self.r), dtype=dtype, device=X.device)
-        buf[:X.shape[0]].copy_(X)
-        return buf
+    def _b_bufs(self, B_k):
+        """The B blocks of the phases: B_k itself in phase 0 (it is only
+        sent, never received into), then two receive buffers in turn.
+        Shifts move maxw rows, so a narrower B_k is copied into a padded
+        buffer first."""
+        if B_k.shape[0] == self.maxw or self.p == 1:
+            first = B_k
+        else:
+            first = torch.zeros((self.maxw, self.r), dtype=self.dtype, device=B_k.device)
+            first[:B_k.shape[0]].copy_(B_k)
+        if self.p == 1:
+            return [first]
+        spare = [torch.empty((self.maxw, self.r), dtype=self.dtype, device=B_k.device)
+                 for _ in range(2)]
+        return [first] + spare
+
+    @staticmethod
+    def _phase_buf(bufs, t):
+        return bufs[0] if t == 0 else bufs[1 + (t - 1) % 2]
 
     def _shift(self, send, recv):
         """send -> rank k - 1, recv <- rank k + 1 (returns a waitable)."""
@@ -200,61 +241,68 @@ class FusedMM15D:
 
     def fusedmm(self, vals, A_k, B_k):
         """FusedMMA rows of this rank: out_i = sum_j s_ij <A_i, B_j> B_j."""
-        out = torch.zeros((self.rows, self.r), dtype=torch.float32, device=A_k.device)
-        bufs = [self._padded(B_k, self.dtype), torch.empty((self.maxw, self.r), dtype=self.dtype,
-                                                            device=A_k.device)]
-        cur = 0
+        out = torch.empty((self.rows, self.r), dtype=torch.float32, device=A_k.device)
+        bufs = self._b_bufs(B_k)
         for t in range(self.p):
             l = self.block_of_phase(t)
+            cur = self._phase_buf(bufs, t)
             # the next block is in flight while this phase computes
-            pend = self._shift(bufs[cur], bufs[1 - cur]) if t + 1 < self.p else []
-            self.ops.fusedmm_acc(self.plans[l], self._vals(vals, l), A_k,
-                                 bufs[cur][:self._width(l)], out)
+            pend = self._shift(cur, self._phase_buf(bufs, t + 1)) if t + 1 < self.p else []
+            # phase 0 writes every output row, later phases add to them
+            call = self.ops.fusedmm if t == 0 else self.ops.fusedmm_acc
+            call(self.plans[l], self._vals(vals, l), A_k, cur[:self._width(l)], out)
             self._wait(pend)
-            cur = 1 - cur
         return out
 
     def fusedmm_t(self, vals, A_k, B_k):
         """FusedMMB rows of this rank's B block: out_j = sum_i s_ij <A_i, B_j> A_i."""
-        bufs = [self._padded(B_k, self.dtype), torch.empty((self.maxw, self.r), dtype=self.dtype,
-                                                            device=A_k.device)]
-        outs = [torch.zeros((self.maxw, self.r), dtype=torch.float32, device=A_k.device),
-                torch.empty((self.maxw, self.r), dtype=torch.float32, device=A_k.device)]
+        dev = A_k.device
+        bufs = self._b_bufs(B_k)
+        outs = [torch.empty((self.maxw, self.r), dtype=torch.float32, device=dev)
+                for _ in range(1 if self.p == 1 else 2)]
         cur = 0
         for t in range(self.p):
             l = self.block_of_phase(t)
-            pend = self._shift(bufs[cur], bufs[1 - cur]) if t + 1 < self.p else []
+            b = self._phase_buf(bufs, t)
+            pend = self._shift(b, self._phase_buf(bufs, t + 1)) if t + 1 < self.p else []
             w = self._width(l)
-            self.ops.fusedmm_t_acc(self.plans[l], self._vals(vals, l), A_k, bufs[cur][:w],
-                                   outs[cur][:w])
-            # the output block travels on with its B block
+            call = self.ops.fusedmm_t if t == 0 else self.ops.fusedmm_t_acc
+            call(self.plans[l], self._vals(vals, l), A_k, b[:w], outs[cur][:w])
+            if self.p == 1:
+                break
+            # the output block travels on with its B block; after p shifts it
+            # is back at its owner
             self._wait(pend + self._shift(outs[cur], outs[1 - cur]))
             cur = 1 - cur
-        return outs[cur][:self._width(self.k)].clone()
+        return outs[cur][:self._width(self.k)]
 
     def fusedmm_bwd(self, vals, A_k, B_k, G_k):
         """Adjoint of FusedMMA for L = <G, FusedMMA>: (dA rows of this rank,
         dB rows of this rank's B block, ds of this rank's nonzeros)."""
         dev = A_k.device
-        dA = torch.zeros((self.rows, self.r), dtype=torch.float32, device=dev)
-        ds = torch.zeros(self.nnz, dtype=torch.float32, device=dev)
-        bufs = [self._padded(B_k, self.dtype), torch.empty((self.maxw, self.r), dtype=self.dtype,
-                                                            device=dev)]
-        dBs = [torch.zeros((self.maxw, self.r), dtype=torch.float32, device=dev),
-               torch.empty((self.maxw, self.r), dtype=torch.float32, device=dev)]
+        dA = torch.empty((self.rows, self.r), dtype=torch.float32, device=dev)
+        ds = torch.empty(self.nnz, dtype=torch.float32, device=dev)
+        bufs = self._b_bufs(B_k)
+        dBs = [torch.empty((self.maxw, self.r), dtype=torch.float32, device=dev)
+               for _ in range(1 if self.p == 1 else 2)]
         cur = 0
         for t in range(self.p):
             l = self.block_of_phase(t)
-            pend = self._shift(bufs[cur], bufs[1 - cur]) if t + 1 < self.p else []
+            b = self._phase_buf(bufs, t)
+            pend = self._shift(b, self._phase_buf(bufs, t + 1)) if t + 1 < self.p else []
             w = self._width(l)
-            sel = self.blocks[l][2]
-            ds_l = torch.empty(sel.numel(), dtype=torch.float32, device=dev)
-            self.ops.fusedmm_bwd_acc(self.plans[l], self._vals(vals, l), A_k, bufs[cur][:w], G_k,
-                                     dA, dBs[cur][:w], ds_l)
-            ds.index_copy_(0, sel, ds_l)
+            sel, span = self.blocks[l][2], self.spans[l]
+            ds_l = (ds.narrow(0, *span) if span is not None
+                    else torch.empty(sel.numel(), dtype=torch.float32, device=dev))
+            call = self.ops.fusedmm_bwd if t == 0 else self.ops.fusedmm_bwd_acc
+            call(self.plans[l], self._vals(vals, l), A_k, b[:w], G_k, dA, dBs[cur][:w], ds_l)
+            if span is None:
+                ds.index_copy_(0, sel, ds_l)
+            if self.p == 1:
+                break
             self._wait(pend + self._shift(dBs[cur], dBs[1 - cur]))
             cur = 1 - cur
-        return dA, dBs[cur][:self._width(self.k)].clone(), ds
+        return dA, dBs[cur][:self._width(self.k)], ds
 
 
 def slice_bounds(r: int, parts: int) -> np.ndarray:

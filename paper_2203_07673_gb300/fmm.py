@@ -289,11 +289,17 @@ def fusedmm_t(plan: Plan, vals, A, B, out=None, stream=None):
     return out
 
 
-def fusedmm_bwd(plan: Plan, vals, A, B, G, need=(True, True, True), stream=None):
-    """Returns (dA, dB, ds) (float32; None where need is False)."""
-    dA = torch.empty((plan.m, plan.r), dtype=torch.float32, device=plan.device) if need[0] else None
-    dB = torch.empty((plan.n, plan.r), dtype=torch.float32, device=plan.device) if need[1] else None
-    ds = torch.empty((plan.nnz,), dtype=torch.float32, device=plan.device) if need[2] else None
+def fusedmm_bwd(plan: Plan, vals, A, B, G, need=(True, True, True), stream=None, out=None):
+    """Returns (dA, dB, ds) (float32; None where need is False).  `out`, if
+    given, is (dA, dB, ds) to write into (None entries are skipped)."""
+    if out is not None:
+        dA, dB, ds = out
+    else:
+        dA = (torch.empty((plan.m, plan.r), dtype=torch.float32, device=plan.device)
+              if need[0] else None)
+        dB = (torch.empty((plan.n, plan.r), dtype=torch.float32, device=plan.device)
+              if need[1] else None)
+        ds = torch.empty((plan.nnz,), dtype=torch.float32, device=plan.device) if need[2] else None
     rc = lib().fmm_fusedmm_bwd(plan.handle, plan._f32(vals, (plan.nnz,), "vals"),
                                plan._dense(A, plan.m, "A"), plan._dense(B, plan.n, "B"),
                                plan._f32(G, (plan.m, plan.r), "G"),

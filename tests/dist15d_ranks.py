@@ -44,6 +44,18 @@ class OracleOps:
     def _np(x):
         return None if x is None else x.detach().cpu().double().numpy()
 
+    def fusedmm(self, plan, vals, A, B, out):
+        out.zero_()
+        self.fusedmm_acc(plan, vals, A, B, out)
+
+    def fusedmm_t(self, plan, vals, A, B, out):
+        out.zero_()
+        self.fusedmm_t_acc(plan, vals, A, B, out)
+
+    def fusedmm_bwd(self, plan, vals, A, B, G, dA, dB, ds):
+        dA.zero_(); dB.zero_()
+        self.fusedmm_bwd_acc(plan, vals, A, B, G, dA, dB, ds)
+
     def fusedmm_acc(self, plan, vals, A, B, out):
         res = self.o.fusedmm(plan["rp"], plan["ci"], self._np(vals), self._np(A), self._np(B),
                              plan["n"])
@@ -101,10 +113,13 @@ def rank_main(rank, world, port, out, seed, r, use_gpu, vals_none):
         d = dist15d.FusedMM15D(rp, ci, S.n, r, torch.float32, ops=ops)
         assert [d.block_of_phase(t) for t in range(world)] == [(rank + t) % world
                                                                for t in range(world)]
+        B_in = Bk.clone()
         res = dict(out=d.fusedmm(vk, Ak, Bk), out_t=d.fusedmm_t(vk, Ak, Bk))
         res["dA"], res["dB"], res["ds"] = d.fusedmm_bwd(vk, Ak, Bk, Gk)
         if use_gpu:
             torch.cuda.synchronize()
+        # the rank's B block is sent in phase 0 but never received into
+        assert torch.equal(Bk, B_in)
         out[rank] = {k: v.cpu().numpy() for k, v in res.items()}
         out[f"bounds{rank}"] = (r0, r1, c0, c1, p0, p1)
         d.close()

@@ -2,9 +2,10 @@
 c = 1) with the library's kernels: two gloo ranks on the one GPU (the
 shifts staged through host memory; no kernel waits on another rank), the
 assembled FusedMMA, FusedMMB, dA, dB and ds against the FP64 oracle on the
-whole matrix, within the float32 parity bar.  Every local call is an
-accumulating one (fmm_fusedmm_acc, fmm_fusedmm_t_acc, fmm_fusedmm_bwd_acc)
-over one column block of the rank's rows."""
+whole matrix, within the float32 parity bar.  Each local call covers one
+column block of the rank's rows: phase 0 writes the outputs (fmm_fusedmm,
+fmm_fusedmm_t, fmm_fusedmm_bwd), later phases add to them (fmm_fusedmm_acc,
+fmm_fusedmm_t_acc, fmm_fusedmm_bwd_acc)."""
 import numpy as np
 import pytest
 
@@ -23,6 +24,41 @@ def test_two_ranks_on_one_gpu_match_the_whole_matrix(r, vals_none):
     got = assemble(res, 2, S, r)
     want = expected(S, None if vals_none else vals, A, B, G)
     for name, x, y in zip(("out", "out_t", "dA", "dB", "ds"), got, want):
+        assert np.all(np.isfinite(x)), name
+        assert rel(x, y) <= 1e-5, name
+
+
+def test_three_ranks_with_a_padded_block():
+    """n = 250 over 3 ranks: blocks of 83, 83 and 84 columns, so two ranks
+    pad their B block to the 84 rows every shift moves."""
+    import dist15d_ranks
+    seed, r = 51, 32
+    S, vals, A, B, G = dist15d_ranks.problem(seed, r=r)
+    res = run_ranks(3, seed, r, use_gpu=True)
+    got = assemble(res, 3, S, r)
+    want = expected(S, vals, A, B, G)
+    for name, x, y in zip(("out", "out_t", "dA", "dB", "ds"), got, want):
+        assert np.all(np.isfinite(x)), name
+        assert rel(x, y) <= 1e-5, name
+
+
+def test_one_rank_without_a_process_group_on_the_gpu():
+    """p = 1: one phase of write-mode calls, B and the values used in place."""
+    import torch
+    import dist15d_ranks
+    from paper_2203_07673_gb300 import dist15d
+    S, vals, A, B, G = dist15d_ranks.problem(61, r=64)
+    dev = torch.device("cuda", 0)
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    d = dist15d.FusedMM15D(t(S.row_ptr), t(S.col_idx), S.n, 64, torch.float32)
+    assert d.p == 1 and d.spans == [(0, S.nnz)]
+    V, A_d, B_d, G_d = t(vals), t(A), t(B), t(G)
+    got = (d.fusedmm(V, A_d, B_d), d.fusedmm_t(V, A_d, B_d)) + d.fusedmm_bwd(V, A_d, B_d, G_d)
+    torch.cuda.synchronize()
+    d.close()
+    want = expected(S, vals, A, B, G)
+    for name, x, y in zip(("out", "out_t", "dA", "dB", "ds"), got, want):
+        x = x.double().cpu().numpy()
         assert np.all(np.isfinite(x)), name
         assert rel(x, y) <= 1e-5, name
 
