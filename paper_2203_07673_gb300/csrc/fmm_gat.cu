@@ -45,20 +45,58 @@ struct GatArgs {
 
 __device__ __forceinline__ float leaky(float x, float slope) { return x > 0.f ? x : slope * x; }
 
-// Eight consecutive elements of a row, widened to float: one 32-byte load of
-// float32 or one 16-byte load of bfloat16 (the read-only path for gathered
-// rows).  p must be 32-byte (float) or 16-byte (bfloat16) aligned.
-__device__ __forceinline__ void load8(const float *p, float *f)
-{
-    asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=f"(f[0]), "=f"(f[1]), "=f"(f[2]), "=f"(f[3]), "=f"(f[4]), "=f"(f[5]),
-                   "=f"(f[6]), "=f"(f[7])
-                 : "l"(p));
-}
-__device__ __forceinline__ void load8(const bf16_t *p, float *f)
-{
-    unpack_bf16x8(__ldg(reinterpret_cast<const uint4 *>(p)), f);
-}
+// EPL consecutive elements of a gathered row as loaded (EPL a multiple of
+// 8): float32 rows in registers as floats (32-byte loads), bfloat16 rows kept
+// packed two to a word until use, so a nonzero in flight costs EPL / 2
+// registers (16-byte loads for EPL = 8, 32-byte loads for EPL = 16).  The
+// read-only path; the address must be aligned to the load width.
+template <typename T, int EPL>
+struct GatRaw;
+
+template <int EPL>
+struct GatRaw<float, EPL> {
+    float v[EPL];
+    __device__ __forceinline__ void load(const float *p)
+    {
+#pragma unroll
+        for (int k = 0; k < EPL / 8; ++k)
+            asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                         : "=f"(v[8 * k]), "=f"(v[8 * k + 1]), "=f"(v[8 * k + 2]),
+                           "=f"(v[8 * k + 3]), "=f"(v[8 * k + 4]), "=f"(v[8 * k + 5]),
+                           "=f"(v[8 * k + 6]), "=f"(v[8 * k + 7])
+                         : "l"(p + 8 * k));
+    }
+    __device__ __forceinline__ float get(int t) const { return v[t]; }
+};
+
+template <int EPL>
+struct GatRaw<bf16_t, EPL> {
+    uint32_t w[EPL / 2];
+    __device__ __forceinline__ void load(const bf16_t *p)
+    {
+        if constexpr (EPL % 16 == 0) {
+#pragma unroll
+            for (int k = 0; k < EPL / 16; ++k)
+                asm volatile("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                             : "=r"(w[8 * k]), "=r"(w[8 * k + 1]), "=r"(w[8 * k + 2]),
+                               "=r"(w[8 * k + 3]), "=r"(w[8 * k + 4]), "=r"(w[8 * k + 5]),
+                               "=r"(w[8 * k + 6]), "=r"(w[8 * k + 7])
+                             : "l"(p + 16 * k));
+        } else {
+#pragma unroll
+            for (int k = 0; k < EPL / 8; ++k) {
+                const uint4 q = __ldg(reinterpret_cast<const uint4 *>(p + 8 * k));
+                w[4 * k] = q.x; w[4 * k + 1] = q.y; w[4 * k + 2] = q.z; w[4 * k + 3] = q.w;
+            }
+        }
+    }
+    // element t: the low half of word t / 2 for even t, the high half for odd
+    __device__ __forceinline__ float get(int t) const
+    {
+        return (t & 1) ? __uint_as_float(w[t >> 1] & 0xffff0000u) : __uint_as_float(w[t >> 1] << 16);
+    }
+};
+
 // Eight floats to a 16-byte-aligned address, streaming (written once).
 __device__ __forceinline__ void store8(float *p, const float *f)
 {
@@ -66,20 +104,40 @@ __device__ __forceinline__ void store8(float *p, const float *f)
     __stcs(reinterpret_cast<float4 *>(p) + 1, make_float4(f[4], f[5], f[6], f[7]));
 }
 
-// One row (or chunk) per team of G = R / 8 lanes; lane l holds elements
-// [8 l, 8 l + 8) of the row, all in head 8 l / rh (rh a multiple of 8), so a
-// lane scores each nonzero once for its head.  Online softmax per lane:
-// with d = e - max, exactly one of exp(max_old - max_new) and exp(e - max_new)
-// differs from 1, so one exponential x = exp(-|d|) gives both; when the score
-// does not raise the maximum (the common case, uniform across a head's lanes)
-// the update is acc += x H_j, else acc = x acc + H_j.  U nonzeros per batch,
-// their gathers in flight together.  Capped at 48 registers (5 blocks per
-// SM): 17-20 % faster on GB300 than the uncapped 58.
-template <typename T, int R, int U>
-__global__ void __launch_bounds__(256, 5) gat_kernel(const GatArgs a)
+// Launch shape of the vector path per element type: EPL elements per lane,
+// U nonzeros in flight per batch, MINB blocks of 256 threads per SM (the
+// register cap).  Measured on GB300 (GAT forward, R-MAT 2^22, 4 heads x 32):
+// 16 elements per lane, one nonzero per batch, beat 8 per lane with two
+// (float32 3.39 against 3.65 ms, bfloat16 2.62 against 3.18 ms); heads whose
+// width is a multiple of 8 but not of 16 take the 8-per-lane shape.
+template <typename T>
+struct GatConfig;
+template <>
+struct GatConfig<float> {
+    static constexpr int EPL = 16, U = 1, MINB = 3;
+};
+template <>
+struct GatConfig<bf16_t> {
+    static constexpr int EPL = 16, U = 1, MINB = 5;
+};
+struct GatNarrow {
+    static constexpr int EPL = 8, U = 2, MINB = 5;
+};
+
+// One row (or chunk) per team of G = R / EPL lanes; lane l holds elements
+// [EPL l, EPL l + EPL) of the row, all in head EPL l / rh (rh a multiple of
+// EPL), so a lane scores each nonzero once for its head.  Online softmax per
+// lane: with d = e - max, exactly one of exp(max_old - max_new) and
+// exp(e - max_new) differs from 1, so one exponential x = exp(-|d|) gives
+// both; when the score does not raise the maximum (the common case, uniform
+// across a head's lanes) the update is acc += x H_j, else acc = x acc + H_j.
+// U nonzeros per batch, their gathers in flight together.
+template <typename T, int R, int U, int EPL, int MINB>
+__global__ void __launch_bounds__(256, MINB) gat_kernel(const GatArgs a)
 {
-    constexpr int G = R / 8;
-    static_assert(R % 8 == 0 && G >= 1 && G <= 32 && (G & (G - 1)) == 0, "row layout");
+    constexpr int G = R / EPL;
+    static_assert(EPL % 8 == 0 && R % EPL == 0 && G >= 1 && G <= 32 && (G & (G - 1)) == 0,
+                  "row layout");
     const int lane = threadIdx.x & 31;
     const int lig = lane & (G - 1);
     const long long gid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / G;
@@ -97,12 +155,12 @@ __global__ void __launch_bounds__(256, 5) gat_kernel(const GatArgs a)
         }
     }
     const T *H = static_cast<const T *>(a.H);
-    const int head = (8 * lig) / a.rh;
+    const int head = (EPL * lig) / a.rh;
     const float *g = a.g + head;
     const float fi = active && end > beg ? __ldg(a.f + (size_t)row * a.heads + head) : 0.f;
-    float mx = -INFINITY, l = 0.f, acc[8];
+    float mx = -INFINITY, l = 0.f, acc[EPL];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) acc[e] = 0.f;
+    for (int e = 0; e < EPL; ++e) acc[e] = 0.f;
 
     // The team loads the column indices and values of IB >= 16 consecutive
     // nonzeros at once (K per lane, coalesced) and hands them to its batches
@@ -138,11 +196,12 @@ __global__ void __launch_bounds__(256, 5) gat_kernel(const GatArgs a)
                 jj[u] = __shfl_sync(0xffffffffu, jv, src);
                 sv[u] = __shfl_sync(0xffffffffu, svv, src);
             }
-            float y[U][8], gj[U];
+            GatRaw<T, EPL> y[U];
+            float gj[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 if (jj[u] >= 0) {
-                    load8(H + (size_t)jj[u] * R + 8 * lig, y[u]);
+                    y[u].load(H + (size_t)jj[u] * R + EPL * lig);
                     gj[u] = __ldg(g + (size_t)jj[u] * a.heads);
                 }
             }
@@ -156,12 +215,12 @@ __global__ void __launch_bounds__(256, 5) gat_kernel(const GatArgs a)
                 if (d > 0.f) {
                     l = fmaf(l, x, 1.f);
 #pragma unroll
-                    for (int t = 0; t < 8; ++t) acc[t] = fmaf(acc[t], x, y[u][t]);
+                    for (int t = 0; t < EPL; ++t) acc[t] = fmaf(acc[t], x, y[u].get(t));
                     mx = e;
                 } else {
                     l += x;
 #pragma unroll
-                    for (int t = 0; t < 8; ++t) acc[t] = fmaf(x, y[u][t], acc[t]);
+                    for (int t = 0; t < EPL; ++t) acc[t] = fmaf(x, y[u].get(t), acc[t]);
                 }
             }
         }
@@ -170,18 +229,23 @@ __global__ void __launch_bounds__(256, 5) gat_kernel(const GatArgs a)
         return;
     if (slot >= 0) {
         // a chunk: keep the unnormalised state for the combine kernel
-        float *base = a.partials + (size_t)slot * 3 * R + 8 * lig;
+        float *base = a.partials + (size_t)slot * 3 * R + EPL * lig;
         float mxe[8], le[8];
 #pragma unroll
         for (int t = 0; t < 8; ++t) { mxe[t] = mx; le[t] = l; }
-        store8(base, acc);
-        store8(base + R, mxe);
-        store8(base + 2 * R, le);
+#pragma unroll
+        for (int k = 0; k < EPL / 8; ++k) {
+            store8(base + 8 * k, acc + 8 * k);
+            store8(base + R + 8 * k, mxe);
+            store8(base + 2 * R + 8 * k, le);
+        }
     } else {
         const float inv = l > 0.f ? 1.f / l : 0.f;
 #pragma unroll
-        for (int t = 0; t < 8; ++t) acc[t] *= inv;
-        store8(a.out + (size_t)row * R + 8 * lig, acc);
+        for (int t = 0; t < EPL; ++t) acc[t] *= inv;
+#pragma unroll
+        for (int k = 0; k < EPL / 8; ++k)
+            store8(a.out + (size_t)row * R + EPL * lig + 8 * k, acc + 8 * k);
     }
 }
 
@@ -287,31 +351,44 @@ __global__ void __launch_bounds__(256) gat_project_kernel(int32_t rows, int32_t 
     }
 }
 
-template <typename T, int R, int U>
+template <typename T, int R, typename C>
 cudaError_t launch_gat_vec(const GatArgs &a, cudaStream_t st)
 {
-    constexpr int G = R / 8;
+    constexpr int G = R / C::EPL;
     const long long total = (long long)a.n_chunks + a.n_light;
-    gat_kernel<T, R, U><<<(unsigned)((total * G + 255) / 256), 256, 0, st>>>(a);
+    gat_kernel<T, R, C::U, C::EPL, C::MINB><<<(unsigned)((total * G + 255) / 256), 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 
-// Vector path: 8 elements per lane, 2 nonzeros per batch.
+template <typename T, typename C>
+cudaError_t launch_gat_shape(const GatArgs &a, cudaStream_t st)
+{
+    switch (a.r) {
+    case 32: return launch_gat_vec<T, 32, C>(a, st);
+    case 64: return launch_gat_vec<T, 64, C>(a, st);
+    case 128: return launch_gat_vec<T, 128, C>(a, st);
+    default: return launch_gat_vec<T, 256, C>(a, st);
+    }
+}
+
+// Vector path (r in {32, 64, 128, 256}, out 16-byte aligned):
+// GatConfig<T>::EPL elements per lane when the head width is a multiple of
+// it and H is 32-byte aligned, else 8 per lane when the head width is a
+// multiple of 8 and H is aligned to that shape's loads (32 bytes of float32,
+// 16 of bfloat16); otherwise one warp per row.
 template <typename T>
 cudaError_t launch_gat(const GatArgs &a, bool vec, cudaStream_t st)
 {
     const long long total = (long long)a.n_chunks + a.n_light;
     if (total == 0)
         return cudaSuccess;
-    if (vec && a.rh % 8 == 0) {
-        switch (a.r) {
-        case 32: return launch_gat_vec<T, 32, 2>(a, st);
-        case 64: return launch_gat_vec<T, 64, 2>(a, st);
-        case 128: return launch_gat_vec<T, 128, 2>(a, st);
-        case 256: return launch_gat_vec<T, 256, 2>(a, st);
-        default: break;
-        }
-    }
+    const uintptr_t h = reinterpret_cast<uintptr_t>(a.H);
+    const bool width = a.r == 32 || a.r == 64 || a.r == 128 || a.r == 256;
+    if (vec && width && a.rh % GatConfig<T>::EPL == 0 && (h & 31u) == 0)
+        return launch_gat_shape<T, GatConfig<T>>(a, st);
+    const uintptr_t narrow_align = sizeof(T) == 2 ? 15u : 31u;
+    if (vec && width && a.rh % GatNarrow::EPL == 0 && (h & narrow_align) == 0)
+        return launch_gat_shape<T, GatNarrow>(a, st);
     gat_generic<T><<<(unsigned)((total + 7) / 8), 256, 0, st>>>(a);
     return cudaGetLastError();
 }
@@ -376,11 +453,9 @@ int fmm_gat_forward(const fmm_plan *p, int32_t heads, const float *vals, const f
     a.rh = p->r / heads;
     a.r = p->r;
     a.slope = slope;
-    // the vector path loads 8 elements of H per lane (32 bytes of float32 or
-    // 16 bytes of bfloat16) and stores 16-byte halves of out
-    const uintptr_t h_align = p->dtype == FMM_BF16 ? 15u : 31u;
-    const bool vec = fast_r(p->r) && (reinterpret_cast<uintptr_t>(H) & h_align) == 0 &&
-                     (reinterpret_cast<uintptr_t>(out) & 15u) == 0;
+    // the vector path stores 16-byte pieces of out; launch_gat checks the
+    // alignment of H against the loads of the shape it picks
+    const bool vec = fast_r(p->r) && (reinterpret_cast<uintptr_t>(out) & 15u) == 0;
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = p->dtype == FMM_BF16 ? launch_gat<bf16_t>(a, vec, st)
                                          : launch_gat<float>(a, vec, st);

@@ -27,7 +27,7 @@ def _graph(seed, m=700, hubs=((5, 1500),)):
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16], ids=["f32", "bf16"])
-@pytest.mark.parametrize("heads,rh", [(4, 32), (2, 32), (1, 64), (8, 16), (3, 8), (2, 12)])
+@pytest.mark.parametrize("heads,rh", [(4, 32), (2, 32), (1, 64), (8, 16), (4, 8), (3, 8), (2, 12)])
 def test_gat_forward_matches_oracle(heads, rh, dtype):
     from paper_2203_07673_gb300 import fmm
     S, rng = _graph(heads * 100 + rh)
@@ -117,10 +117,12 @@ def test_registered_values_skip_the_permutation():
     plan.set_values(None)
 
 
-@pytest.mark.parametrize("offset", [4, 8], ids=["16B", "32B"])
-def test_gat_h_alignment(offset):
-    """float32 H rows are loaded 32 bytes per lane: H that is only 16-byte
-    aligned takes the generic kernel; both must match the oracle."""
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16], ids=["f32", "bf16"])
+@pytest.mark.parametrize("offset_bytes", [16, 32], ids=["16B", "32B"])
+def test_gat_h_alignment(offset_bytes, dtype):
+    """H rows are loaded 32 bytes at a time: H that is only 16-byte aligned
+    takes the generic kernel (float32) or the 8-per-lane shape with 16-byte
+    loads (bfloat16); every path must match the oracle."""
     from paper_2203_07673_gb300 import fmm
     S, rng = _graph(21, m=400)
     heads, rh = 4, 32
@@ -128,13 +130,16 @@ def test_gat_h_alignment(offset):
     H = (rng.standard_normal((S.n, r)) * 0.5).astype(np.float32)
     f = rng.standard_normal((S.m, heads)).astype(np.float32)
     g = rng.standard_normal((S.n, heads)).astype(np.float32)
-    buf = torch.zeros(S.n * r + 8, device="cuda")
-    buf[offset:offset + S.n * r] = torch.from_numpy(H).reshape(-1).cuda()
+    esz = torch.tensor([], dtype=dtype).element_size()
+    offset = offset_bytes // esz
+    buf = torch.zeros(S.n * r + 64 // esz, device="cuda", dtype=dtype)
+    Hd = torch.from_numpy(H).to(dtype)
+    buf[offset:offset + S.n * r] = Hd.reshape(-1).cuda()
     Ht = buf[offset:offset + S.n * r].view(S.n, r)
-    assert (Ht.data_ptr() % 32 == 0) == (offset == 8)
+    assert (Ht.data_ptr() % 32 == 0) == (offset_bytes == 32)
     rp, ci = torch.from_numpy(S.row_ptr).cuda(), torch.from_numpy(S.col_idx).cuda()
-    plan = fmm.Plan(rp, ci, S.n, r, split_nnz=256)
+    plan = fmm.Plan(rp, ci, S.n, r, dtype, split_nnz=256)
     out = fmm.gat_forward(plan, heads, None, torch.from_numpy(f).cuda(),
                           torch.from_numpy(g).cuda(), Ht, 0.2)
-    ref = oracle.gat(S.row_ptr, S.col_idx, None, f, g, H.astype(np.float64), heads, 0.2)
+    ref = oracle.gat(S.row_ptr, S.col_idx, None, f, g, Hd.double().numpy(), heads, 0.2)
     assert relF(out.double().cpu().numpy(), ref) <= 1e-5
