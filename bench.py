@@ -776,13 +776,13 @@ def zipf_section(args, dev, stream):
 
 
 def run_dist15d(args, rank, world, local_rank):
-    """1.5D dense-shifting FusedMM with local kernel fusion (Algorithm 1,
-    c = 1) over the ranks, weak-scaled like the paper's Erdos-Renyi setup:
-    each rank owns 2^20 rows (times --scale) of an ER pattern with 32
-    distinct uniform columns per row over all N x 2^20 columns, r = 128,
-    FP32, s ~ U(0,1), A, B ~ N(0, 1/128), drawn on its device.  A step is
-    FusedMMA + FusedMMB over the whole matrix (p phases each); units
-    2 * nnz * r of the whole matrix per step."""
+    """1.5D dense-shifting FusedMM with local kernel fusion (Algorithm 1)
+    over the ranks, replication factor --dist-c, weak-scaled like the
+    paper's Erdos-Renyi setup: each rank owns 2^20 rows (times --scale) of
+    an ER pattern with 32 distinct uniform columns per row over all
+    N x 2^20 columns, r = 128, FP32, s ~ U(0,1), A, B ~ N(0, 1/128), drawn
+    on its device.  A step is FusedMMA + FusedMMB over the whole matrix
+    (N / c phases each); units 2 * nnz * r of the whole matrix per step."""
     import torch
     import torch.distributed as dist
 
@@ -794,13 +794,26 @@ def run_dist15d(args, rank, world, local_rank):
     rows = max(1, int((1 << 20) * args.scale))
     n = rows * world
     r = 128
-    g = wl._torch_gen(dev, (wl.ROOT_SEED + 2) * 1000003 + 15 + rank)
-    rp, ci = wl.er_exact_degree_torch(rows, n, 32, g, dev)
-    vals = torch.rand(ci.numel(), generator=g, device=dev)
+    c = args.dist_c
+    if c < 1 or world % c:
+        raise SystemExit(f"--dist-c {c} must divide the {world} ranks")
+    lp = world // c
+    layer, q = divmod(rank, lp)
+    bounds = [l * rows for l in range(world + 1)]
+    # the fiber's c row blocks are drawn alike by its c ranks (one seed per
+    # fiber); each keeps the columns of its layer's B blocks
+    g = wl._torch_gen(dev, (wl.ROOT_SEED + 2) * 1000003 + 15 + q)
+    rp_f, ci_f = wl.er_exact_degree_torch(c * rows, n, 32, g, dev)
+    vals_f = torch.rand(ci_f.numel(), generator=g, device=dev)
+    rp, ci, slots = dist15d.local_block(rp_f, ci_f, 0, c * rows, bounds[layer * lp],
+                                        bounds[(layer + 1) * lp])
+    vals = vals_f.index_select(0, slots)
+    del rp_f, ci_f, vals_f, slots
+    g = wl._torch_gen(dev, (wl.ROOT_SEED + 2) * 1000003 + 7919 + rank)
     A = torch.randn(rows, r, generator=g, device=dev) * (1.0 / 128) ** 0.5
     B = torch.randn(rows, r, generator=g, device=dev) * (1.0 / 128) ** 0.5
-    d = dist15d.FusedMM15D(rp, ci, n, r, torch.float32,
-                           col_bounds=[l * rows for l in range(world + 1)])
+    d = dist15d.FusedMM15D(rp, ci, n, r, torch.float32, col_bounds=bounds, c=c,
+                           row_bounds=bounds)
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -844,7 +857,14 @@ def run_dist15d(args, rank, world, local_rank):
     e1.record(stream)
     barrier()
     e2e_ms = reduce_max([e0.elapsed_time(e1) / reps], dev, world)[0]
-    nnz_total = 32 * rows * world
+    h2d_local = (A_h.numel() + B_h.numel() + v_h.numel()) * 4
+    if world > 1:
+        t = torch.tensor([float(h2d_local)], device=dev, dtype=torch.float64)
+        dist.all_reduce(t)
+        h2d_total = int(t.item())
+    else:
+        h2d_total = h2d_local
+    nnz_total = 32 * rows * world   # every row of S holds 32 nonzeros
     units = 2.0 * nnz_total * r
     # library launches per step: per phase one FusedMMA pass (+ its combine
     # where rows are split) and one FusedMMB pass (+ combine) after the value
@@ -862,13 +882,14 @@ def run_dist15d(args, rank, world, local_rank):
             "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": elapsed / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"1.5D dense shifting + local kernel fusion (Algorithm 1, c = 1): "
-                                   f"ER {n}x{n}, 32 nnz/row, r=128, FP32, {rows} rows per rank",
+            "config": {"workload": f"1.5D dense shifting + local kernel fusion (Algorithm 1, "
+                                   f"c = {c}): ER {n}x{n}, 32 nnz/row, r=128, FP32, {rows} rows "
+                                   f"per rank",
                        "m": n, "n": n, "nnz": nnz_total, "r": r,
                        "step": "FusedMMA + FusedMMB over the whole matrix",
-                       "parallelism": f"1.5D ring x{world}"},
+                       "parallelism": f"1.5D grid {lp}x{c}"},
             "e2e": {"value": units / (e2e_ms / 1e3), "unit": UNIT,
-                    "h2d_bytes_per_step": (A_h.numel() + B_h.numel() + v_h.numel()) * 4 * world,
+                    "h2d_bytes_per_step": h2d_total,
                     "d2h_bytes_per_step": 2 * rows * r * 4 * world, "ms_per_step": e2e_ms},
             "gpu_launches": per_step * args.steps, "clocks": clk}), flush=True)
     return 0
@@ -1382,6 +1403,8 @@ def main():
     ap.add_argument("--dist15d", action="store_true",
                     help="1.5D dense-shifting FusedMM over the ranks (weak-scaled ER, 2^20 rows "
                          "per rank); without it N > 1 runs independent replicas")
+    ap.add_argument("--dist-c", type=int, default=1,
+                    help="replication factor of --dist15d (divides N)")
     ap.add_argument("--zipf-only", action="store_true",
                     help="only the Zipf-row (c4) section, printed as one JSON object")
     ap.add_argument("--no-library", action="store_true",

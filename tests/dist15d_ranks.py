@@ -73,6 +73,14 @@ class OracleOps:
         dB += torch.from_numpy(gb).to(dB.dtype)
         ds.copy_(torch.from_numpy(gs).to(ds.dtype))
 
+    def sddmm(self, plan, vals, A, B, v):
+        v.zero_()
+        self.sddmm_acc(plan, vals, A, B, v)
+
+    def spmm_acc(self, plan, v, B, out):
+        res = self.o.spmm(plan["rp"], plan["ci"], self._np(v), self._np(B), plan["n"])
+        out += torch.from_numpy(res).to(out.dtype)
+
     def sddmm_acc(self, plan, vals, A, B, v):
         res = self.o.sddmm(plan["rp"], plan["ci"], self._np(vals), self._np(A), self._np(B),
                            plan["n"])
@@ -90,7 +98,9 @@ class OracleOps:
         pass
 
 
-def rank_main(rank, world, port, out, seed, r, use_gpu, vals_none):
+def rank_main(rank, world, port, out, seed, r, use_gpu, vals_none, c=1):
+    """FusedMM15D on the (world/c) x c grid: the rank's local S = S[T_q, C_l],
+    A block q c + l, B block l (world/c) + q."""
     import torch.distributed as dist
     from paper_2203_07673_gb300 import dist15d
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
@@ -99,20 +109,23 @@ def rank_main(rank, world, port, out, seed, r, use_gpu, vals_none):
         S, vals, A, B, G = problem(seed, r=r)
         rb = dist15d.row_bounds_by_nnz(S.row_ptr, world)
         cb = dist15d.col_bounds_uniform(S.n, world)
-        r0, r1 = int(rb[rank]), int(rb[rank + 1])
-        c0, c1 = int(cb[rank]), int(cb[rank + 1])
-        p0, p1 = int(S.row_ptr[r0]), int(S.row_ptr[r1])
+        lp = world // c
+        layer, q = divmod(rank, lp)
+        a, b = q * c + layer, layer * lp + q
+        rp_l, ci_l, slots = dist15d.local_block(
+            torch.from_numpy(S.row_ptr), torch.from_numpy(S.col_idx), int(rb[q * c]),
+            int(rb[(q + 1) * c]), int(cb[layer * lp]), int(cb[(layer + 1) * lp]))
+        r0, r1, c0, c1 = int(rb[a]), int(rb[a + 1]), int(cb[b]), int(cb[b + 1])
         dev = torch.device("cuda", 0) if use_gpu else torch.device("cpu")
-        rp = torch.from_numpy((S.row_ptr[r0:r1 + 1].astype(np.int64) - p0).astype(np.int32)).to(dev)
-        ci = torch.from_numpy(S.col_idx[p0:p1].copy()).to(dev)
-        vk = None if vals_none else torch.from_numpy(vals[p0:p1].copy()).to(dev)
+        rp, ci = rp_l.to(dev), ci_l.to(dev)
+        vk = None if vals_none else torch.from_numpy(vals[slots.numpy()]).to(dev)
         Ak = torch.from_numpy(A[r0:r1].copy()).to(dev)
         Bk = torch.from_numpy(B[c0:c1].copy()).to(dev)
         Gk = torch.from_numpy(G[r0:r1].copy()).to(dev)
         ops = None if use_gpu else OracleOps()
-        d = dist15d.FusedMM15D(rp, ci, S.n, r, torch.float32, ops=ops)
-        assert [d.block_of_phase(t) for t in range(world)] == [(rank + t) % world
-                                                               for t in range(world)]
+        d = dist15d.FusedMM15D(rp, ci, S.n, r, torch.float32, ops=ops, c=c, row_bounds=rb)
+        assert [d.block_of_phase(t) for t in range(lp)] == [layer * lp + (q + t) % lp
+                                                            for t in range(lp)]
         B_in = Bk.clone()
         res = dict(out=d.fusedmm(vk, Ak, Bk), out_t=d.fusedmm_t(vk, Ak, Bk))
         res["dA"], res["dB"], res["ds"] = d.fusedmm_bwd(vk, Ak, Bk, Gk)
@@ -121,7 +134,45 @@ def rank_main(rank, world, port, out, seed, r, use_gpu, vals_none):
         # the rank's B block is sent in phase 0 but never received into
         assert torch.equal(Bk, B_in)
         out[rank] = {k: v.cpu().numpy() for k, v in res.items()}
-        out[f"bounds{rank}"] = (r0, r1, c0, c1, p0, p1)
+        out[f"bounds{rank}"] = (r0, r1, c0, c1, slots.numpy())
+        d.close()
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def reuse_rank_main(rank, world, port, out, seed, r, use_gpu, vals_none, c=1):
+    """ReplicationReuse15D on the (world/c) x c grid: the rank's local S =
+    S[R_l, C_q], A block l (world/c) + q, B block q c + l."""
+    import torch.distributed as dist
+    from paper_2203_07673_gb300 import dist15d
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        S, vals, A, B, G = problem(seed, r=r)
+        rb = dist15d.row_bounds_by_nnz(S.row_ptr, world)
+        cb = dist15d.col_bounds_uniform(S.n, world)
+        lp = world // c
+        layer, q = divmod(rank, lp)
+        a, b = layer * lp + q, q * c + layer
+        rp_l, ci_l, slots = dist15d.local_block(
+            torch.from_numpy(S.row_ptr), torch.from_numpy(S.col_idx), int(rb[layer * lp]),
+            int(rb[(layer + 1) * lp]), int(cb[q * c]), int(cb[(q + 1) * c]))
+        r0, r1, c0, c1 = int(rb[a]), int(rb[a + 1]), int(cb[b]), int(cb[b + 1])
+        dev = torch.device("cuda", 0) if use_gpu else torch.device("cpu")
+        vk = None if vals_none else torch.from_numpy(vals[slots.numpy()]).to(dev)
+        Ak = torch.from_numpy(A[r0:r1].copy()).to(dev)
+        Bk = torch.from_numpy(B[c0:c1].copy()).to(dev)
+        ops = None if use_gpu else OracleOps()
+        d = dist15d.ReplicationReuse15D(rp_l.to(dev), ci_l.to(dev), S.n, r, torch.float32,
+                                        row_bounds=rb, c=c, ops=ops)
+        A_in = Ak.clone()
+        res = dict(out=d.fusedmm(vk, Ak, Bk))
+        if use_gpu:
+            torch.cuda.synchronize()
+        assert torch.equal(Ak, A_in)
+        out[rank] = {k: v.cpu().numpy() for k, v in res.items()}
+        out[f"bounds{rank}"] = (r0, r1)
         d.close()
         dist.barrier()
     finally:

@@ -27,14 +27,15 @@ def free_port():
         return s.getsockname()[1]
 
 
-def run_ranks(world, seed, r, use_gpu, vals_none=False, body="rank_main"):
+def run_ranks(world, seed, r, use_gpu, vals_none=False, body="rank_main", c=None):
     import dist15d_ranks
     ctx = mp.get_context("spawn")
     mgr = ctx.Manager()
     out = mgr.dict()
     port = free_port()
+    extra = () if c is None else (c,)
     procs = [ctx.Process(target=getattr(dist15d_ranks, body),
-                         args=(k, world, port, out, seed, r, use_gpu, vals_none))
+                         args=(k, world, port, out, seed, r, use_gpu, vals_none) + extra)
              for k in range(world)]
     for p in procs:
         p.start()
@@ -45,12 +46,17 @@ def run_ranks(world, seed, r, use_gpu, vals_none=False, body="rank_main"):
 
 
 def assemble(res, world, S, r):
+    """Every rank's output blocks into whole matrices; each row, column and
+    nonzero must come from exactly one rank."""
     out = np.zeros((S.m, r)); out_t = np.zeros((S.n, r))
     dA = np.zeros((S.m, r)); dB = np.zeros((S.n, r)); ds = np.zeros(S.nnz)
+    seen_r, seen_c, seen_nz = np.zeros(S.m, int), np.zeros(S.n, int), np.zeros(S.nnz, int)
     for k in range(world):
-        r0, r1, c0, c1, p0, p1 = res[f"bounds{k}"]
-        out[r0:r1] = res[k]["out"]; dA[r0:r1] = res[k]["dA"]; ds[p0:p1] = res[k]["ds"]
+        r0, r1, c0, c1, slots = res[f"bounds{k}"]
+        out[r0:r1] = res[k]["out"]; dA[r0:r1] = res[k]["dA"]; ds[slots] = res[k]["ds"]
         out_t[c0:c1] = res[k]["out_t"]; dB[c0:c1] = res[k]["dB"]
+        seen_r[r0:r1] += 1; seen_c[c0:c1] += 1; seen_nz[slots] += 1
+    assert np.all(seen_r == 1) and np.all(seen_c == 1) and np.all(seen_nz == 1)
     return out, out_t, dA, dB, ds
 
 
@@ -111,6 +117,74 @@ def test_ring_schedule_matches_the_whole_matrix(world, vals_none):
     want = expected(S, None if vals_none else vals, A, B, G)
     for name, x, y in zip(("out", "out_t", "dA", "dB", "ds"), got, want):
         assert rel(x, y) <= 1e-6, name
+
+
+@pytest.mark.parametrize("world,c", [(2, 2), (4, 2), (4, 4)])
+def test_replicated_grid_matches_the_whole_matrix(world, c):
+    """Algorithm 1 with replication factor c: A all-gathered along each fiber
+    of c ranks, B shifted around layers of world / c ranks, the FusedMMA
+    output and dA reduce-scattered along the fiber."""
+    import dist15d_ranks
+    seed, r = 5 + world + c, 8
+    S, vals, A, B, G = dist15d_ranks.problem(seed, r=r)
+    res = run_ranks(world, seed, r, use_gpu=False, c=c)
+    got = assemble(res, world, S, r)
+    want = expected(S, vals, A, B, G)
+    for name, x, y in zip(("out", "out_t", "dA", "dB", "ds"), got, want):
+        assert rel(x, y) <= 1e-6, name
+
+
+@pytest.mark.parametrize("world,c", [(2, 1), (3, 1), (2, 2), (4, 2), (4, 4)])
+@pytest.mark.parametrize("vals_none", [False, True])
+def test_replication_reuse_matches_the_whole_matrix(world, c, vals_none):
+    """FusedMMA by replication reuse: B all-gathered once along the fiber,
+    an SDDMM round with A travelling, an SpMM round with the output
+    travelling; no reduce-scatter."""
+    import dist15d_ranks
+    seed, r = 61 + 3 * world + c, 8
+    S, vals, A, B, G = dist15d_ranks.problem(seed, r=r)
+    res = run_ranks(world, seed, r, use_gpu=False, vals_none=vals_none, body="reuse_rank_main",
+                    c=c)
+    out = np.zeros((S.m, r))
+    seen = np.zeros(S.m, int)
+    for k in range(world):
+        r0, r1 = res[f"bounds{k}"]
+        out[r0:r1] = res[k]["out"]
+        seen[r0:r1] += 1
+    assert np.all(seen == 1)
+    want = expected(S, None if vals_none else vals, A, B, G)[0]
+    assert rel(out, want) <= 1e-6
+
+
+def test_local_blocks_of_the_grid_partition_s():
+    """The local S of every rank of a (p/c) x c grid, for both layouts,
+    together hold every nonzero exactly once, with its row and column."""
+    rng = np.random.default_rng(7)
+    S = wl.random_csr(300, 170, rng, mean_deg=7, dup_frac=0.1, unsorted=True,
+                      hubs=((4, 150),))
+    rp, ci = torch.from_numpy(S.row_ptr), torch.from_numpy(S.col_idx)
+    row_of = np.repeat(np.arange(S.m), S.degrees())
+    for p, c in ((4, 2), (6, 3), (6, 2), (5, 1)):
+        rb, cb = dist15d.row_bounds_by_nnz(S.row_ptr, p), dist15d.col_bounds_uniform(S.n, p)
+        lp = p // c
+        for layout in ("lkf", "reuse"):
+            seen = np.zeros(S.nnz, int)
+            for k in range(p):
+                layer, q = divmod(k, lp)
+                if layout == "lkf":
+                    rr = (int(rb[q * c]), int(rb[(q + 1) * c]))
+                    cc = (int(cb[layer * lp]), int(cb[(layer + 1) * lp]))
+                else:
+                    rr = (int(rb[layer * lp]), int(rb[(layer + 1) * lp]))
+                    cc = (int(cb[q * c]), int(cb[(q + 1) * c]))
+                lrp, lci, slots = dist15d.local_block(rp, ci, *rr, *cc)
+                slots = slots.numpy()
+                seen[slots] += 1
+                assert np.array_equal(lci.numpy(), S.col_idx[slots])
+                lrow = np.repeat(np.arange(rr[1] - rr[0]), np.diff(lrp.numpy().astype(np.int64)))
+                assert np.array_equal(lrow + rr[0], row_of[slots])
+                assert np.all((S.col_idx[slots] >= cc[0]) & (S.col_idx[slots] < cc[1]))
+            assert np.all(seen == 1), (p, c, layout)
 
 
 def test_one_rank_without_a_process_group():

@@ -76,3 +76,34 @@ def test_sparse_shifting_two_ranks_on_one_gpu(r):
     for name, x, y in zip(("out", "out_t"), got, want):
         assert np.all(np.isfinite(x)), name
         assert rel(x, y) <= 1e-5, name
+
+
+def test_replicated_grid_four_ranks_on_one_gpu():
+    """Algorithm 1 with replication factor 2 on a 2 x 2 grid: four gloo ranks
+    on the one GPU, A all-gathered and the FusedMMA output and dA
+    reduce-scattered along each fiber (staged through host memory)."""
+    import dist15d_ranks
+    seed, r = 71, 32
+    S, vals, A, B, G = dist15d_ranks.problem(seed, r=r)
+    res = run_ranks(4, seed, r, use_gpu=True, c=2)
+    got = assemble(res, 4, S, r)
+    want = expected(S, vals, A, B, G)
+    for name, x, y in zip(("out", "out_t", "dA", "dB", "ds"), got, want):
+        assert np.all(np.isfinite(x)), name
+        assert rel(x, y) <= 1e-5, name
+
+
+@pytest.mark.parametrize("world,c", [(2, 1), (4, 2)])
+def test_replication_reuse_on_one_gpu(world, c):
+    """FusedMMA by replication reuse (fmm_sddmm per A block held, then
+    fmm_spmm / fmm_spmm_acc into the travelling output blocks)."""
+    import dist15d_ranks
+    seed, r = 81 + world, 32
+    S, vals, A, B, G = dist15d_ranks.problem(seed, r=r)
+    res = run_ranks(world, seed, r, use_gpu=True, body="reuse_rank_main", c=c)
+    out = np.zeros((S.m, r))
+    for k in range(world):
+        r0, r1 = res[f"bounds{k}"]
+        out[r0:r1] = res[k]["out"]
+    assert np.all(np.isfinite(out))
+    assert rel(out, expected(S, vals, A, B, G)[0]) <= 1e-5
