@@ -1243,6 +1243,44 @@ def run_als(args, rank, world, local_rank):
     return 0
 
 
+def run_probe(args, dev):
+    """Gather ceilings (fmm_probe_gather): the rate at which a stream of
+    uniform random row indices fetches rows of a table and nothing else,
+    for tables from L2-resident to far beyond L2, rows of 128 and 256 bytes
+    (BF16 and FP32 rows of r = 64), 80M indices (the Zipf-row workload's
+    nonzero count), CUDA events over 10 launches after 3 warm-ups."""
+    import torch
+
+    from paper_2203_07673_gb300 import fmm
+
+    count = int(80_000_000 * args.scale)
+    g = torch.Generator(device=dev)
+    g.manual_seed(2203_07673)
+    rows_out = []
+    for mib in (32, 64, 128, 512, 2048):
+        for row_bytes in (128, 256):
+            rows = (mib << 20) // row_bytes
+            table = torch.randn(rows, row_bytes // 4, device=dev, generator=g)
+            idx = torch.randint(0, rows, (count,), device=dev, dtype=torch.int32, generator=g)
+            sink = torch.zeros(1, dtype=torch.int32, device=dev)
+            for _ in range(3):
+                fmm.probe_gather(table, idx, sink)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(10):
+                fmm.probe_gather(table, idx, sink)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 10
+            rows_out.append({"table_MiB": mib, "row_bytes": row_bytes, "ms": ms,
+                             "rows_per_s": count / (ms / 1e3),
+                             "gathered_GBs": count * row_bytes / (ms / 1e3) / 1e9})
+            del table, idx
+    return {"probe": "fmm_probe_gather, uniform random row indices", "indices": count,
+            "rows": rows_out}
+
+
 def run_gat(args, rank, world, local_rank):
     """Graph-attention forward (Sec. VI-E) on an R-MAT 2^22 graph (avg degree
     16, the workload-3 recipe drawn on the device), `--heads` heads of
@@ -1407,6 +1445,8 @@ def main():
                     help="replication factor of --dist15d (divides N)")
     ap.add_argument("--zipf-only", action="store_true",
                     help="only the Zipf-row (c4) section, printed as one JSON object")
+    ap.add_argument("--probe", action="store_true",
+                    help="gather ceilings of uniform random rows, tables of 32 MiB to 2 GiB")
     ap.add_argument("--no-library", action="store_true",
                     help="skip the cuSPARSE (torch.sparse) comparison")
     args = ap.parse_args()
@@ -1428,6 +1468,14 @@ def main():
         dev = torch.device("cuda", local_rank)
         torch.cuda.set_device(dev)
         res = zipf_section(args, dev, torch.cuda.current_stream())
+        if rank == 0:
+            print(json.dumps(res), flush=True)
+        rc = 0
+    elif args.probe:
+        import torch
+        dev = torch.device("cuda", local_rank)
+        torch.cuda.set_device(dev)
+        res = run_probe(args, dev)
         if rank == 0:
             print(json.dumps(res), flush=True)
         rc = 0
