@@ -30,6 +30,7 @@ int sm_count()
 }
 
 static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+static bool aligned32(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 31u) == 0; }
 
 // Variant codes: vectors-per-lane multiple * 100 + groups per team * 10 +
 // nonzeros per group per batch (the combinations instantiated in
@@ -115,7 +116,8 @@ cudaError_t launch_pass(int mode, int dtype, const KernelVariant &v, const PassA
         if (e != cudaErrorNotSupported)
             return e;
     }
-    if (v.ring > 0 && vec && fwd) {
+    // the register-ring pass loads gathered rows 32 bytes at a time
+    if (v.ring > 0 && vec && fwd && aligned32(a.Y)) {
         const cudaError_t e = dtype == FMM_BF16
                                   ? launch_pipe_bf16(mode, v.vpl_mult, v.u, v.ring, v.mb, v.refill, a, st)
                                   : launch_pipe_f32(mode, v.vpl_mult, v.u, v.ring, v.mb, v.refill, a, st);

@@ -28,6 +28,13 @@
 // past the end of a row get value 0 and a zero row, so every batch runs the
 // same instructions and contributes exactly nothing.
 //
+// Row layout: with two or more 16-byte words per lane, a lane owns
+// consecutive words of a row (lane l: words l VPL ... l VPL + VPL - 1), so a
+// gathered row reaches the lane in 32-byte loads (ld.global.nc.v8.b32) and
+// each load instruction of the warp touches one 128-byte line per bfloat16
+// row of r = 64, where word-interleaved 16-byte loads touch every line twice.
+// The gathered operand must be 32-byte aligned.
+//
 // Roles: FusedMM, SDDMM, SpMM (instantiated), and the two adjoint passes:
 // over S (two dot products of the gathered row, against the local row and
 // the local float32 gradient row; ds written) and over S^T (the gathered row
@@ -43,6 +50,16 @@ namespace fmm {
 
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
+// Two consecutive 16-byte words of a row from a 32-byte-aligned address, by
+// one 32-byte load on the read-only path.
+__device__ __forceinline__ void load32(const void *p, uint4 &w0, uint4 &w1)
+{
+    asm volatile("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(w0.x), "=r"(w0.y), "=r"(w0.z), "=r"(w0.w), "=r"(w1.x), "=r"(w1.y),
+                   "=r"(w1.z), "=r"(w1.w)
+                 : "l"(p));
+}
 
 // The 16-byte word q of a row of T as float pairs (element 2i, 2i + 1).
 template <typename T>
@@ -81,10 +98,13 @@ __global__ void __launch_bounds__(256, MB) pipe_pass_kernel(const PassArgs a)
     constexpr bool GATHER_H = MODE == M_BWD_COL;   // float32 gradient row, gathered
     constexpr int HW = GATHER_H ? VPL * EPV / 4 : 1;   // float4 words of a gathered H row
     constexpr int ND = TWO ? 2 * U : U;                // dot products per batch
+    constexpr bool WIDE = VPL % 2 == 0;                // lane-contiguous words, 32-byte loads
 
     const int lane = threadIdx.x & 31;
     const int lig = lane & (G - 1);
     const int tbase = lane & ~(G - 1);
+    // the row word that word v of this lane holds
+    auto widx = [lig](int v) { return WIDE ? lig * VPL + v : v * G + lig; };
     const long long gid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / G;
     const long long total = (long long)a.n_chunks + a.n_light;
     const bool active = gid < total;
@@ -110,7 +130,7 @@ __global__ void __launch_bounds__(256, MB) pipe_pass_kernel(const PassArgs a)
         for (int v = 0; v < VPL; ++v)
 #pragma unroll
             for (int q = 0; q < EPV / 4; ++q) {
-                const float4 x = ld.f4(hrow + (v * G + lig) * EPV + 4 * q, gather);
+                const float4 x = ld.f4(hrow + widx(v) * EPV + 4 * q, gather);
                 f[v * W2 + 2 * q] = make_float2(x.x, x.y);
                 f[v * W2 + 2 * q + 1] = make_float2(x.z, x.w);
             }
@@ -121,7 +141,7 @@ __global__ void __launch_bounds__(256, MB) pipe_pass_kernel(const PassArgs a)
     if (HAS_L && active && end > beg) {
 #pragma unroll
         for (int v = 0; v < VPL; ++v) {
-            const uint4 q = ld.u4(reinterpret_cast<const uint4 *>(L + (size_t)row * R) + v * G + lig,
+            const uint4 q = ld.u4(reinterpret_cast<const uint4 *>(L + (size_t)row * R) + widx(v),
                                   false);
             unpack2<T>(q, &l2[v * W2]);
         }
@@ -164,12 +184,23 @@ __global__ void __launch_bounds__(256, MB) pipe_pass_kernel(const PassArgs a)
         for (int u = 0; u < U; ++u) {
             const int t = bb * U + u;
             const int jj = __shfl_sync(0xffffffffu, j[t / G], tbase + (t % G));
+            if constexpr (WIDE) {
 #pragma unroll
-            for (int v = 0; v < VPL; ++v) {
-                dst[u][v] = make_uint4(0u, 0u, 0u, 0u);
-                if (jj >= 0)
-                    dst[u][v] = ld.u4(reinterpret_cast<const uint4 *>(Y + (size_t)jj * R) + v * G + lig,
-                                      true);
+                for (int v = 0; v < VPL; v += 2) {
+                    dst[u][v] = make_uint4(0u, 0u, 0u, 0u);
+                    dst[u][v + 1] = make_uint4(0u, 0u, 0u, 0u);
+                    if (jj >= 0)
+                        load32(reinterpret_cast<const uint4 *>(Y + (size_t)jj * R) + widx(v),
+                               dst[u][v], dst[u][v + 1]);
+                }
+            } else {
+#pragma unroll
+                for (int v = 0; v < VPL; ++v) {
+                    dst[u][v] = make_uint4(0u, 0u, 0u, 0u);
+                    if (jj >= 0)
+                        dst[u][v] = ld.u4(reinterpret_cast<const uint4 *>(Y + (size_t)jj * R) + widx(v),
+                                          true);
+                }
             }
         }
     };
@@ -186,7 +217,7 @@ __global__ void __launch_bounds__(256, MB) pipe_pass_kernel(const PassArgs a)
                     dst[u][v * (EPV / 4) + q] = make_float4(0.f, 0.f, 0.f, 0.f);
                     if (jj >= 0)
                         dst[u][v * (EPV / 4) + q] =
-                            ld.f4(a.H + (size_t)jj * R + (v * G + lig) * EPV + 4 * q, true);
+                            ld.f4(a.H + (size_t)jj * R + widx(v) * EPV + 4 * q, true);
                 }
         }
     };
@@ -356,7 +387,7 @@ __global__ void __launch_bounds__(256, MB) pipe_pass_kernel(const PassArgs a)
                 for (int v = 0; v < VPL; ++v) {
 #pragma unroll
                     for (int w = 0; w < W2; w += 2) {
-                        const int k = (v * G + lig) * EPV + 2 * w;
+                        const int k = widx(v) * EPV + 2 * w;
                         const float2 p0 = acc2[v * W2 + w], p1 = acc2[v * W2 + w + 1];
                         out_store4(ld, dst + k, make_float4(p0.x, p0.y, p1.x, p1.y),
                                    a.accumulate && slot < 0);

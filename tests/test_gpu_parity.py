@@ -246,6 +246,42 @@ def test_misaligned_pointers_take_generic_path():
     assert_close("misaligned fusedmm", got, ref, mag, r, deg_max(S))
 
 
+@pytest.mark.parametrize("variant", [32212, 22212])
+def test_ring_pass_needs_32_byte_rows(variant):
+    """The register-ring pass loads gathered rows 32 bytes at a time: with
+    A and B 16-byte but not 32-byte aligned (BF16, r = 64) the call takes the
+    team kernel; aligned or not, FusedMMA and FusedMMB match the oracle."""
+    from paper_2203_07673_gb300 import fmm
+    S, _ = pattern("hubs", 5)
+    rng = np.random.default_rng(2)
+    r = 64
+    A = rng.standard_normal((S.m, r)).astype(np.float32)
+    B = rng.standard_normal((S.n, r)).astype(np.float32)
+    vals = rng.uniform(0.5, 1.5, S.nnz).astype(np.float32)
+    rp, ci, vt, _, _ = upload(S, vals, A, B)
+    Ab = torch.from_numpy(A).to(torch.bfloat16)
+    Bb = torch.from_numpy(B).to(torch.bfloat16)
+    A64, B64 = Ab.double().numpy(), Bb.double().numpy()
+    ref = oracle.fusedmm(S.row_ptr, S.col_idx, vals, A64, B64, S.n)
+    mag = oracle.fusedmm(S.row_ptr, S.col_idx, vals, np.abs(A64), np.abs(B64), S.n)
+    ref_t = oracle.fusedmm_t(S.row_ptr, S.col_idx, vals, A64, B64, S.n)
+    mag_t = oracle.fusedmm_t(S.row_ptr, S.col_idx, vals, np.abs(A64), np.abs(B64), S.n)
+    plan = fmm.Plan(rp, ci, S.n, r, torch.bfloat16, variant=variant)
+    for off in (0, 8):   # bf16 elements: 0 or 16 bytes past a 512-byte boundary
+        Abuf = torch.zeros(S.m * r + 16, dtype=torch.bfloat16, device="cuda")
+        Bbuf = torch.zeros(S.n * r + 16, dtype=torch.bfloat16, device="cuda")
+        Abuf[off:off + S.m * r] = Ab.reshape(-1).cuda()
+        Bbuf[off:off + S.n * r] = Bb.reshape(-1).cuda()
+        At = Abuf[off:off + S.m * r].view(S.m, r)
+        Bt = Bbuf[off:off + S.n * r].view(S.n, r)
+        assert (At.data_ptr() % 32 == 0) == (off == 0) and At.data_ptr() % 16 == 0
+        assert_close(f"ring fusedmm off={off}", fmm.fusedmm(plan, vt, At, Bt), ref, mag, r,
+                     deg_max(S))
+        assert_close(f"ring fusedmm_t off={off}", fmm.fusedmm_t(plan, vt, At, Bt), ref_t, mag_t,
+                     r, int(np.bincount(S.col_idx, minlength=S.n).max()))
+    plan.close()
+
+
 def test_all_ones_pattern_matches_dense_gemm():
     # dense pattern, s = 1: FusedMMA = A (B^T B), FusedMMB = B (A^T A)
     from paper_2203_07673_gb300 import fmm
