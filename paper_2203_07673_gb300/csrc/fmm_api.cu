@@ -116,8 +116,9 @@ cudaError_t launch_pass(int mode, int dtype, const KernelVariant &v, const PassA
         if (e != cudaErrorNotSupported)
             return e;
     }
-    // the register-ring pass loads gathered rows 32 bytes at a time
-    if (v.ring > 0 && vec && fwd && aligned32(a.Y)) {
+    // the register-ring pass loads gathered rows 32 bytes at a time; of the
+    // adjoint roles it has the pass over S
+    if (v.ring > 0 && vec && (fwd || mode == M_BWD_ROW) && aligned32(a.Y)) {
         const cudaError_t e = dtype == FMM_BF16
                                   ? launch_pipe_bf16(mode, v.vpl_mult, v.u, v.ring, v.mb, v.refill, a, st)
                                   : launch_pipe_f32(mode, v.vpl_mult, v.u, v.ring, v.mb, v.refill, a, st);
@@ -125,8 +126,8 @@ cudaError_t launch_pass(int mode, int dtype, const KernelVariant &v, const PassA
             return e;
         // a ring layout this width does not have: the team kernel below
     }
-    // backward roles of a staged, pipelined or bulk-staged plan: the team
-    // kernel's default layout for the width
+    // other backward roles of a staged, pipelined or bulk-staged plan: the
+    // team kernel's default layout for the width
     const KernelVariant t =
         (v.stages > 0 || v.ring > 0 || v.depth > 0) ? team_default_variant(a.r, dtype) : v;
     if (dtype == FMM_BF16)

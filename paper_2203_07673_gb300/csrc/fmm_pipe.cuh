@@ -35,13 +35,14 @@
 // row of r = 64, where word-interleaved 16-byte loads touch every line twice.
 // The gathered operand must be 32-byte aligned.
 //
-// Roles: FusedMM, SDDMM, SpMM (instantiated), and the two adjoint passes:
-// over S (two dot products of the gathered row, against the local row and
-// the local float32 gradient row; ds written) and over S^T (the gathered row
-// and its float32 gradient row both in the ring).  The adjoint roles are not
-// instantiated: on R-MAT 2^22 with bfloat16 rows of r = 64 they took 5.4-5.6
-// ms for the backward against 5.2 ms with the team kernel.  One team of G
-// lanes per row or chunk of a split row.
+// Roles: FusedMM, SDDMM, SpMM, and the two adjoint passes: over S (two
+// dot products of the gathered row, against the local row and the local
+// float32 gradient row; ds written) and over S^T (the gathered row and its
+// float32 gradient row both in the ring).  The pass over S is instantiated
+// for the default layout only (code 32212): on R-MAT 2^22 with bfloat16 rows
+// of r = 64 the backward took 5.205 ms with it against 5.289 ms with the
+// team kernel; the pass over S^T (5.47 ms with it) is not instantiated.  One
+// team of G lanes per row or chunk of a split row.
 #pragma once
 
 #include "fmm_rows.cuh"
@@ -122,7 +123,9 @@ __global__ void __launch_bounds__(256, MB) pipe_pass_kernel(const PassArgs a)
         l2[e] = make_float2(0.f, 0.f);
         acc2[e] = make_float2(0.f, 0.f);
     }
-    h2[0] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int e = 0; e < (LOCAL_H ? E2 : 1); ++e)
+        h2[e] = make_float2(0.f, 0.f);   // rows without nonzeros never load theirs
     // a float32 row in T's element mapping (word v of the lane holds EPV
     // elements): EPV / 4 float4 per word
     auto load_h = [&](const float *hrow, float2 *f, bool gather) {
@@ -437,7 +440,7 @@ cudaError_t dispatch_pipe(int mode, int vpl, int u, int ring, int mb, int refill
     FMM_PIPE_MODES(2 * B, 1, 2, 2, 0)
     FMM_PIPE_MODES(2 * B, 1, 2, 3, 0)
     FMM_PIPE_MODES(2 * B, 1, 4, 2, 0)
-    FMM_PIPE_MODES(2 * B, 1, 2, 2, 1)
+    FMM_PIPE_MODES(2 * B, 1, 2, 2, 1) FMM_PIPE(M_BWD_ROW, 2 * B, 1, 2, 2, 1)
     FMM_PIPE_MODES(B, 2, 2, 4, 0)
     FMM_PIPE_MODES(B, 2, 2, 4, 1)
     FMM_PIPE_MODES(B, 2, 4, 3, 0)

@@ -646,7 +646,8 @@ KernelVariant default_variant(int32_t r, int32_t dtype, double avg_nnz)
     // as it is read (code 32212).  Measured on GB300 (FusedMMA / FusedMMB
     // pass, ms): Zipf rows 2^21 x 2^19 1.71 / 1.54 -> 1.36 / 1.06, R-MAT 2^22
     // 1.65 -> 1.41, Erdos-Renyi 2^20 at r = 128 1.55 / 1.74 -> 1.41 / 1.53.
-    // Its backward roles run the team kernel with the same lane layout.
+    // Of the backward roles, the pass over S runs the same ring pass, the pass
+    // over S^T the team kernel's default layout.
     if (dtype == FMM_BF16 && (r == 64 || r == 128)) {
         v.vpl_mult = 2;
         v.u = 1;
