@@ -45,6 +45,7 @@ KERNEL_SOURCES = [os.path.join(ROOT, "paper_2203_07673_gb300", "csrc", f)
                   for f in ("fmm_rows.cuh", "fmm_rows_f32.cu", "fmm_rows_bf16.cu",
                             "fmm_staged.cuh", "fmm_staged_f32.cu", "fmm_staged_bf16.cu",
                             "fmm_pipe.cuh", "fmm_pipe_f32.cu", "fmm_pipe_bf16.cu",
+                            "fmm_stream.cuh", "fmm_stream_f32.cu", "fmm_stream_bf16.cu",
                             "fmm_internal.cuh", "fmm_plan.cu")]
 
 

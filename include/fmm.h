@@ -126,12 +126,23 @@ typedef struct fmm_plan_options {
                                  each gathered row into a ring of D slots
                                  in shared memory with one bulk copy
                                  (cp.async.bulk, mbarrier completion), M
-                                 resident blocks per SM.  With these last
-                                 three kinds the backward passes run the
-                                 width's default team layout (112 for
-                                 bfloat16 rows, 212 for float32 rows of at
-                                 most 32 vectors).  A layout a width does
-                                 not have falls back to that team layout.
+                                 resident blocks per SM; or 50000 + M*1000
+                                 + P*100 + 10 + V (52212, 52412, 54211):
+                                 FusedMM, SDDMM and SpMM walk runs of
+                                 consecutive rows (at most 256 nonzeros and
+                                 64 rows each, cut by the plan) as one
+                                 stream of nonzeros with the register ring
+                                 of the F = 3 kind running across row
+                                 boundaries.  With these kinds the backward
+                                 pass over S^T, and the pass over S except
+                                 for 32212 and 52212 (which run it with the
+                                 register ring of 32212), run the width's
+                                 default team layout (112 for bfloat16
+                                 rows, 212 for float32 rows of at most 32
+                                 vectors).  The register-ring and streaming
+                                 kinds need the gathered operand 32-byte
+                                 aligned.  A layout a width does not have
+                                 falls back to that team layout.
                                  Default: 32212 for bfloat16 rows of r = 64
                                  and 128, 1042 for float32 rows of r = 128,
                                  else that team layout                       */

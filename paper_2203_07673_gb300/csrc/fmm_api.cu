@@ -40,13 +40,18 @@ static bool aligned32(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 
 // blocks per SM * 1000 + register-ring batches * 100 + nonzeros per batch *
 // 10 + vectors-per-lane multiple for the pipelined pass (fmm_pipe.cuh);
 // 40000 + resident blocks per SM * 1000 + ring slots * 10 + vectors-per-lane
-// multiple for the bulk-staged pass (fmm_bulk.cuh).  The
-// backward roles of staged, pipelined and bulk-staged codes run the team
-// kernel in the width's default layout (team_default_variant).
+// multiple for the bulk-staged pass (fmm_bulk.cuh); 50000 + resident blocks
+// per SM * 1000 + register-ring batches * 100 + 10 + vectors-per-lane
+// multiple for the streaming pass (fmm_stream.cuh, one nonzero per batch,
+// refill order).  The backward roles of staged and bulk-staged codes run
+// the team kernel in the width's default layout (team_default_variant);
+// pipelined and streaming codes run the adjoint pass over S by the
+// pipelined pass of the same ring (where instantiated) and the pass over
+// S^T by the team kernel.
 static const int kVariantCodes[] = {114, 118, 222, 224, 441, 442, 214, 124, 112, 122, 212, 221,
                                     1041, 1042, 1081, 1082,
                                     22212, 23212, 22412, 32212, 24221, 34221, 23421, 23241,
-                                    44042, 43082, 44041, 44081};
+                                    44042, 43082, 44041, 44081, 52212, 52412, 54211};
 
 bool variant_known(int code)
 {
@@ -58,6 +63,16 @@ bool variant_known(int code)
 KernelVariant decode_variant(int code)
 {
     KernelVariant v;
+    if (code >= 50000) {
+        v.stream = 1;
+        v.refill = 1;
+        v.mb = (code / 1000) % 10;
+        v.ring = (code / 100) % 10;
+        v.u = 1;
+        v.vpl_mult = code % 10;
+        v.ng = 1;
+        return v;
+    }
     if (code >= 40000) {
         v.mb = (code / 1000) % 10;
         v.depth = (code / 10) % 100;
@@ -90,6 +105,8 @@ KernelVariant decode_variant(int code)
 
 int encode_variant(const KernelVariant &v)
 {
+    if (v.stream)
+        return 50000 + v.mb * 1000 + v.ring * 100 + 10 + v.vpl_mult;
     if (v.depth > 0)
         return 40000 + v.mb * 1000 + v.depth * 10 + v.vpl_mult;
     if (v.ring > 0)
@@ -108,6 +125,13 @@ cudaError_t launch_pass(int mode, int dtype, const KernelVariant &v, const PassA
     if (v.stages > 0 && vec && fwd) {
         return dtype == FMM_BF16 ? launch_staged_bf16(mode, v.vpl_mult, v.stages, a, st)
                                  : launch_staged_f32(mode, v.vpl_mult, v.stages, a, st);
+    }
+    if (v.stream && vec && fwd && aligned32(a.Y)) {
+        const cudaError_t e = dtype == FMM_BF16
+                                  ? launch_stream_bf16(mode, v.vpl_mult, v.ring, v.mb, a, st)
+                                  : launch_stream_f32(mode, v.vpl_mult, v.ring, v.mb, a, st);
+        if (e != cudaErrorNotSupported)
+            return e;
     }
     if (v.depth > 0 && vec && fwd) {
         const cudaError_t e = dtype == FMM_BF16
@@ -194,6 +218,8 @@ int run_pass(const fmm_plan *p, const Side &side, int mode, const float *s, cons
     a.chunks = side.chunks;
     a.n_chunks = side.n_chunks;
     a.partials = side.partials;
+    a.runs = side.runs;
+    a.n_runs = side.n_runs;
     a.s = s;
     a.s_direct = 0;
     a.L = L;

@@ -22,6 +22,9 @@ struct KernelVariant {
     int refill = 0;   // pipelined pass: 1 = refill a slot as soon as it is read
     int depth = 0;    // > 0: the bulk-staged pass (fmm_bulk.cuh), this many row
                       // slots in shared memory per team (forward roles)
+    int stream = 0;   // 1: the streaming pass (fmm_stream.cuh): a team walks a run
+                      // of consecutive rows as one stream of nonzeros, with the
+                      // register ring of the pipelined pass (ring, mb; refill)
 };
 
 // One side of a plan: the CSR that a row pass walks (S itself, or S^T with a
@@ -39,6 +42,9 @@ struct Side {
     int4 *chunks = nullptr;           // {row, begin, end, unused} per chunk
     int32_t n_chunks = 0;
     int4 *split = nullptr;            // {row, first chunk, chunk count, unused}
+    int2 *runs = nullptr;             // {first row, end row}: runs of consecutive
+                                      // light rows for the streaming pass
+    int32_t n_runs = 0;
     float *partials = nullptr;        // 3 x n_chunks x r floats: partial rows (and
                                       // the attention pass's softmax states)
     int32_t max_nnz = 0;              // longest row
@@ -94,6 +100,8 @@ struct PassArgs {
     const int4 *chunks;
     int32_t n_chunks;
     float *partials;
+    const int2 *runs = nullptr;  // runs of consecutive light rows (streaming pass)
+    int32_t n_runs = 0;
     // operands
     const float *s;            // per-nonzero scalars (NULL = 1): in S order, or in
                                // this CSR's order when s_direct is set
@@ -133,6 +141,15 @@ cudaError_t launch_bulk_bf16(int mode, int vpl_mult, int depth, int mb, const Pa
                              cudaStream_t st);
 cudaError_t launch_pipe_f32(int mode, int vpl_mult, int u, int ring, int mb, int refill,
                             const PassArgs &a, cudaStream_t st);
+cudaError_t launch_stream_f32(int mode, int vpl_mult, int ring, int mb, const PassArgs &a,
+                              cudaStream_t st);
+cudaError_t launch_stream_bf16(int mode, int vpl_mult, int ring, int mb, const PassArgs &a,
+                               cudaStream_t st);
+// Runs of the streaming pass: consecutive light rows with at most this many
+// nonzeros together (a longer light row is a run of its own) and at most
+// kRunRows rows.
+constexpr int32_t kRunNnz = 256;
+constexpr int32_t kRunRows = 64;
 cudaError_t launch_pipe_bf16(int mode, int vpl_mult, int u, int ring, int mb, int refill,
                              const PassArgs &a, cudaStream_t st);
 // dst[q] = src[perm[q]] for q < nnz (values of S into the order of S^T).

@@ -77,11 +77,18 @@ __device__ __forceinline__ void unpack2(const uint4 q, float2 *f)
     }
 }
 
-// MB is the number of 256-thread blocks a variant asks to keep resident per
-// SM (a register cap of 65536 / (256 MB) per thread): the register ring
-// trades rows in flight per team against teams per SM.
+// Blocks of one warp: a block retires when its slowest row is done, so
+// small blocks let the SM start new rows as soon as a warp is free (GB300,
+// against 256-thread blocks: FusedMMA on Zipf rows 1.341 -> 1.294 ms, R-MAT
+// forward 1.416 -> 1.345 ms; 64-thread blocks 1.302 / 1.352).
+constexpr int kPipeBlock = 32;
+
+// MB is the number of 256 threads a variant asks to keep resident per SM,
+// as 256 / kPipeBlock blocks each (a register cap of 65536 / (256 MB) per
+// thread): the register ring trades rows in flight per team against teams
+// per SM.
 template <int MODE, typename T, int R, int VPL, int U, int RING, int MB, int REFILL>
-__global__ void __launch_bounds__(256, MB) pipe_pass_kernel(const PassArgs a)
+__global__ void __launch_bounds__(kPipeBlock, MB * (256 / kPipeBlock)) pipe_pass_kernel(const PassArgs a)
 {
     static_assert(MODE >= M_FUSED && MODE <= M_BWD_COL, "role");
     using TS = TeamShape<T, R, VPL, 1>;
@@ -406,8 +413,8 @@ cudaError_t launch_pipe(const PassArgs &a, cudaStream_t st)
 {
     constexpr int G = TeamShape<T, R, VPL, 1>::G;
     const long long total = (long long)a.n_chunks + a.n_light;
-    const long long blocks = (total * G + 255) / 256;
-    pipe_pass_kernel<MODE, T, R, VPL, U, RING, MB, REFILL><<<(unsigned)blocks, 256, 0, st>>>(a);
+    const long long blocks = (total * G + kPipeBlock - 1) / kPipeBlock;
+    pipe_pass_kernel<MODE, T, R, VPL, U, RING, MB, REFILL><<<(unsigned)blocks, kPipeBlock, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -358,6 +358,60 @@ static cudaError_t dmalloc(P **p, size_t count, fmm_plan *plan)
         }                                                            \
     } while (0)
 
+// Runs of the streaming pass (host, once per side): consecutive light rows
+// (at most split_nnz nonzeros) taken greedily in index order while the run
+// stays within kRunNnz nonzeros and kRunRows rows; a split row ends a run
+// and belongs to none (its chunks are work items of their own).  Runs are
+// ordered by nonzero count, longest first (stable), so the teams of one warp
+// walk streams of similar length.
+static int build_runs(Side &side, const int32_t *row_ptr, int32_t rows, int32_t split_nnz,
+                      cudaStream_t st, fmm_plan *plan)
+{
+    std::vector<int32_t> rp((size_t)rows + 1);
+    FMM_TRY(cudaMemcpyAsync(rp.data(), row_ptr, sizeof(int32_t) * ((size_t)rows + 1),
+                            cudaMemcpyDeviceToHost, st), "read row pointers");
+    FMM_TRY(cudaStreamSynchronize(st), "plan sync");
+    std::vector<int2> runs;
+    std::vector<int32_t> nnz;
+    int32_t start = -1, count = 0, rows_in = 0;
+    auto close = [&](int32_t end) {
+        if (start >= 0) {
+            runs.push_back(make_int2(start, end));
+            nnz.push_back(count);
+        }
+        start = -1; count = 0; rows_in = 0;
+    };
+    for (int32_t i = 0; i < rows; ++i) {
+        const int32_t d = rp[i + 1] - rp[i];
+        if (d > split_nnz) {
+            close(i);
+            continue;
+        }
+        if (start >= 0 && (count + d > kRunNnz || rows_in == kRunRows))
+            close(i);
+        if (start < 0)
+            start = i;
+        count += d;
+        ++rows_in;
+    }
+    close(rows);
+    std::vector<int32_t> idx(runs.size());
+    for (size_t k = 0; k < idx.size(); ++k)
+        idx[k] = (int32_t)k;
+    std::stable_sort(idx.begin(), idx.end(), [&](int32_t x, int32_t y) { return nnz[x] > nnz[y]; });
+    std::vector<int2> sorted(runs.size());
+    for (size_t k = 0; k < idx.size(); ++k)
+        sorted[k] = runs[idx[k]];
+    side.n_runs = (int32_t)sorted.size();
+    if (side.n_runs == 0)
+        return FMM_OK;
+    FMM_TRY(dmalloc(&side.runs, sorted.size(), plan), "allocate runs");
+    FMM_TRY(cudaMemcpyAsync(side.runs, sorted.data(), sizeof(int2) * sorted.size(),
+                            cudaMemcpyHostToDevice, st), "upload runs");
+    FMM_TRY(cudaStreamSynchronize(st), "plan sync");
+    return FMM_OK;
+}
+
 static int build_side(Side &side, const int32_t *row_ptr, int32_t rows, int32_t split_nnz,
                       int32_t r, Temps &tmp, cudaStream_t st, fmm_plan *plan)
 {
@@ -404,6 +458,11 @@ static int build_side(Side &side, const int32_t *row_ptr, int32_t rows, int32_t 
         for (int k = 0; k <= key; ++k)
             side.bucket_start[k] = 0;
     }
+    {
+        const int rc = build_runs(side, row_ptr, rows, split_nnz, st, plan);
+        if (rc != FMM_OK)
+            return rc;
+    }
     if (side.n_split == 0)
         return FMM_OK;
     int2 *d_ranges = nullptr;
@@ -448,6 +507,7 @@ static int build_side(Side &side, const int32_t *row_ptr, int32_t rows, int32_t 
 static void free_side(Side &s)
 {
     cudaFree(s.order); cudaFree(s.chunks); cudaFree(s.split); cudaFree(s.partials);
+    cudaFree(s.runs);
     s = Side();
 }
 
@@ -686,7 +746,7 @@ int32_t default_split_nnz(int64_t nnz, int32_t r, int32_t dtype, const KernelVar
         const int vpl = (vecs > 32 ? vecs / 32 : 1) * v.vpl_mult;
         lanes = std::min(32, std::max(1, vecs / std::max(1, vpl)) * std::max(1, v.ng));
     }
-    const int warps = (v.ring > 0 || v.depth > 0) && v.mb > 0 ? 8 * v.mb : 32;
+    const int warps = (v.ring > 0 || v.depth > 0 || v.stream) && v.mb > 0 ? 8 * v.mb : 32;
     const int64_t teams = (int64_t)sm_count() * warps * (32 / lanes);
     return (int32_t)std::min<int64_t>(8192, std::max<int64_t>(256, nnz / (4 * teams)));
 }

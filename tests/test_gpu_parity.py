@@ -110,9 +110,10 @@ def test_kernel_variants(r, dtype, split_nnz, variant):
     run_all(S, {"split_nnz": split_nnz, "variant": variant}, r, dtype, seed=3)
 
 
-# the register-ring (2xxxx, 3xxxx) and bulk-staged (4xxxx) forward passes
+# the register-ring (2xxxx, 3xxxx), bulk-staged (4xxxx) and streaming (5xxxx)
+# forward passes
 PIPELINED_AND_BULK = [22212, 23212, 22412, 32212, 24221, 34221, 23421, 23241,
-                      44042, 43082, 44041, 44081]
+                      44042, 43082, 44041, 44081, 52212, 52412, 54211]
 
 
 @pytest.mark.parametrize("variant", PIPELINED_AND_BULK)
@@ -246,7 +247,7 @@ def test_misaligned_pointers_take_generic_path():
     assert_close("misaligned fusedmm", got, ref, mag, r, deg_max(S))
 
 
-@pytest.mark.parametrize("variant", [32212, 22212])
+@pytest.mark.parametrize("variant", [32212, 22212, 52212])
 def test_ring_pass_needs_32_byte_rows(variant):
     """The register-ring pass loads gathered rows 32 bytes at a time: with
     A and B 16-byte but not 32-byte aligned (BF16, r = 64) the call takes the
@@ -412,7 +413,8 @@ def test_rows_without_nonzeros_are_zeroed():
     deg, cdeg = S.degrees(), np.bincount(S.col_idx, minlength=S.n)
     assert (deg == 0).sum() > 50 and (cdeg == 0).sum() > 20
     rng = np.random.default_rng(2)
-    for r, code in ((32, 0), (128, 0), (64, 1082), (24, 0), (64, 32212), (64, 44042)):
+    for r, code in ((32, 0), (128, 0), (64, 1082), (24, 0), (64, 32212), (64, 44042),
+                    (64, 52212), (128, 54211)):
         A = rng.standard_normal((S.m, r)).astype(np.float32)
         B = rng.standard_normal((S.n, r)).astype(np.float32)
         vals = rng.uniform(0, 1, S.nnz).astype(np.float32)
@@ -444,7 +446,7 @@ def test_rows_without_nonzeros_are_zeroed():
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16], ids=["f32", "bf16"])
-@pytest.mark.parametrize("variant", [0, 212, 1042, 32212, 44042])
+@pytest.mark.parametrize("variant", [0, 212, 1042, 32212, 44042, 52212])
 @pytest.mark.parametrize("r", [32, 128, 24])
 def test_accumulating_calls_add_to_the_output(r, variant, dtype):
     """fmm_fusedmm_acc / _t_acc / _bwd_acc and fmm_sddmm_acc / _spmm_acc /
