@@ -227,8 +227,10 @@ class Grid15D:
             return []
         dst = self.rank_of((self.q - 1) % self.lp, self.layer)
         src = self.rank_of((self.q + 1) % self.lp, self.layer)
-        if self.gloo and send.is_cuda:
-            s_h, r_h = send.cpu(), torch.empty(recv.shape, dtype=recv.dtype)
+        if self.gloo and (send.is_cuda or send.dtype == torch.bfloat16):
+            # staged through host memory, as raw bytes (gloo moves no bfloat16)
+            s_h = _as_bytes(send.cpu())
+            r_h = torch.empty(s_h.shape, dtype=torch.uint8)
             reqs = dist.batch_isend_irecv([
                 dist.P2POp(dist.isend, s_h, dst, group=self.group),
                 dist.P2POp(dist.irecv, r_h, src, group=self.group)])
@@ -244,7 +246,7 @@ class Grid15D:
             for q in reqs:
                 q.wait()
             if r_h is not None:
-                recv.copy_(r_h)
+                recv.copy_(r_h.view(recv.dtype).view(recv.shape))
 
     def gather_fiber(self, X, counts):
         """All-gather along the fiber: the rows of the c blocks (block l of
@@ -257,13 +259,14 @@ class Grid15D:
         buf[:X.shape[0]].copy_(X)
         host = self.gloo and X.is_cuda
         src = buf.cpu() if host else buf
-        if src.dtype == torch.bfloat16:
-            src = src.view(torch.int16)           # moved as bytes
+        raw = self.gloo and X.dtype == torch.bfloat16
+        if raw:
+            src = _as_bytes(src)                  # gloo moves no bfloat16: raw bytes
         parts = [torch.empty_like(src) for _ in range(self.c)]
         dist.all_gather(parts, src, group=self.fiber_group)
+        if raw:
+            parts = [q.view(X.dtype).view(buf.shape) for q in parts]
         T = torch.cat([parts[l][:int(counts[l])] for l in range(self.c)])
-        if X.dtype == torch.bfloat16:
-            T = T.view(torch.bfloat16)
         return T.to(X.device)
 
     def reduce_scatter_fiber(self, T, offs):
@@ -280,6 +283,11 @@ class Grid15D:
             if l == self.layer:
                 mine = blk
         return mine.to(T.device)
+
+
+def _as_bytes(t):
+    """A contiguous tensor's bytes as a flat uint8 tensor (same storage)."""
+    return t.contiguous().view(-1).view(torch.uint8)
 
 
 def _phase_buf(bufs, t):

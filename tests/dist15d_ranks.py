@@ -98,9 +98,10 @@ class OracleOps:
         pass
 
 
-def rank_main(rank, world, port, out, seed, r, use_gpu, vals_none, c=1):
+def rank_main(rank, world, port, out, seed, r, use_gpu, vals_none, c=1, bf16=False):
     """FusedMM15D on the (world/c) x c grid: the rank's local S = S[T_q, C_l],
-    A block q c + l, B block l (world/c) + q."""
+    A block q c + l, B block l (world/c) + q; with bf16, A and B in bfloat16
+    (the blocks moved along fibers and rings as raw bytes)."""
     import torch.distributed as dist
     from paper_2203_07673_gb300 import dist15d
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
@@ -119,11 +120,12 @@ def rank_main(rank, world, port, out, seed, r, use_gpu, vals_none, c=1):
         dev = torch.device("cuda", 0) if use_gpu else torch.device("cpu")
         rp, ci = rp_l.to(dev), ci_l.to(dev)
         vk = None if vals_none else torch.from_numpy(vals[slots.numpy()]).to(dev)
-        Ak = torch.from_numpy(A[r0:r1].copy()).to(dev)
-        Bk = torch.from_numpy(B[c0:c1].copy()).to(dev)
+        dt = torch.bfloat16 if bf16 else torch.float32
+        Ak = torch.from_numpy(A[r0:r1].copy()).to(dev).to(dt)
+        Bk = torch.from_numpy(B[c0:c1].copy()).to(dev).to(dt)
         Gk = torch.from_numpy(G[r0:r1].copy()).to(dev)
         ops = None if use_gpu else OracleOps()
-        d = dist15d.FusedMM15D(rp, ci, S.n, r, torch.float32, ops=ops, c=c, row_bounds=rb)
+        d = dist15d.FusedMM15D(rp, ci, S.n, r, dt, ops=ops, c=c, row_bounds=rb)
         assert [d.block_of_phase(t) for t in range(lp)] == [layer * lp + (q + t) % lp
                                                             for t in range(lp)]
         B_in = Bk.clone()

@@ -107,3 +107,20 @@ def test_replication_reuse_on_one_gpu(world, c):
         out[r0:r1] = res[k]["out"]
     assert np.all(np.isfinite(out))
     assert rel(out, expected(S, vals, A, B, G)[0]) <= 1e-5
+
+
+def test_replicated_grid_bf16_on_one_gpu():
+    """BF16 A and B on a 2 x 2 grid with the library's kernels: blocks
+    gathered and shifted as raw bytes, FP32 outputs against the oracle on
+    the BF16-rounded inputs within the FP32 bar."""
+    import torch
+    import dist15d_ranks
+    seed, r = 91, 64
+    S, vals, A, B, G = dist15d_ranks.problem(seed, r=r)
+    res = run_ranks(4, seed, r, use_gpu=True, c=2, bf16=True)
+    got = assemble(res, 4, S, r)
+    rnd = lambda X: torch.from_numpy(X).to(torch.bfloat16).float().numpy()  # noqa: E731
+    want = expected(S, vals, rnd(A), rnd(B), G)
+    for name, x, y in zip(("out", "out_t", "dA", "dB", "ds"), got, want):
+        assert np.all(np.isfinite(x)), name
+        assert rel(x, y) <= 1e-5, name
