@@ -3,9 +3,12 @@
 A variant code V*100 + N*10 + U fixes how a row pass maps onto the GPU:
 V vectors per lane (with the row width, the lanes per dense row, i.e. the
 r-tiling), N lane groups sharing one output row (with V, the rows per warp)
-and U nonzeros per group per batch.  ``tune_plan`` times every candidate on
-the plan's own operands with CUDA events and keeps the fastest, separately
-for the passes over S and over S^T.  ``tune_batch`` groups the items of a
+and U nonzeros per group per batch; the staged (1xxx), register-ring
+(2xxxx, 3xxxx) and streaming (5xxxx) codes keep gathered rows in flight in
+shared memory or registers (include/fmm.h lists them).  ``tune_plan`` times
+every candidate, and the plan's current codes, on the plan's own operands
+with CUDA events and keeps the fastest, separately for the passes over S
+and over S^T.  ``tune_batch`` groups the items of a
 batch by a signature of their shape (r, dtype, average and largest row
 length, as powers of two), tunes one item per group and applies the result
 to the group; results can be cached in a JSON file keyed by the signature.
@@ -20,7 +23,8 @@ import torch
 
 from . import fmm
 
-ALL_CODES = (112, 114, 118, 122, 124, 212, 214, 221, 222, 224, 441, 442, 1041, 1042, 1081, 1082)
+ALL_CODES = (112, 114, 118, 122, 124, 212, 214, 221, 222, 224, 441, 442, 1041, 1042, 1081, 1082,
+             22212, 22412, 32212, 52412)
 BATCH_CODES = (112, 114, 122, 212, 214, 221)
 
 
@@ -55,8 +59,8 @@ def tune_plan(plan: fmm.Plan, vals, A, B, G=None, candidates=ALL_CODES, iters=5,
     m, n, r = plan.m, plan.n, plan.r
     out = torch.empty(m, r, device=plan.device)
     out_t = torch.empty(n, r, device=plan.device)
-    lib, sp = fmm.lib(), torch.cuda.current_stream().cuda_stream
     if backward and G is not None:
+        lib, sp = fmm.lib(), torch.cuda.current_stream().cuda_stream
         dA = torch.empty(m, r, device=plan.device)
         dB = torch.empty(n, r, device=plan.device)
         ds = torch.empty(plan.nnz, device=plan.device)
@@ -77,8 +81,10 @@ def tune_plan(plan: fmm.Plan, vals, A, B, G=None, candidates=ALL_CODES, iters=5,
         def t_side():
             fmm.fusedmm_t(plan, vals, A, B, out=out_t)
 
+    info = plan.info()
+    current = (info["variant"], info["variant_t"])
     times_s, times_t = {}, {}
-    for code in candidates:
+    for code in dict.fromkeys(tuple(candidates) + current):
         plan.set_variant(code, code)
         times_s[code] = _time(s_side, iters)
         times_t[code] = _time(t_side, iters)

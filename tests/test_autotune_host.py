@@ -85,3 +85,54 @@ def test_cache_round_trip(monkeypatch, tmp_path):
                         cache_path=str(path))
     assert tuned2 == {"r64-bf16": 221} and fresh[0]["plan"].code == 221
     assert calls == [{64: 221}]
+
+
+class FakeRowPlan:
+    """A plan for tune_plan: FP32 rows, current codes (variant, variant_t)."""
+
+    def __init__(self, current=(32212, 1042)):
+        self.m, self.n, self.r, self.nnz = 8, 6, 4, 10
+        self.device = torch.device("cpu")
+        self.current = current
+        self.code = None
+        self.set_calls = []
+
+    def info(self):
+        return {"variant": self.current[0], "variant_t": self.current[1]}
+
+    def set_variant(self, v, vt):
+        self.set_calls.append((v, vt))
+        self.code = v
+
+
+def test_tune_plan_times_the_current_codes_and_keeps_the_fastest(monkeypatch):
+    """The plan's current codes are timed with the candidates, so tuning
+    never returns a slower variant than the one the plan had; each side
+    keeps its own fastest code."""
+    plan = FakeRowPlan()
+    s_cost = {32212: 1.0, 112: 1.5, 212: 1.2}       # the current S code is fastest
+    t_cost = {1042: 2.0, 22412: 1.8, 212: 2.5}      # a candidate beats the current S^T code
+
+    def fake_time(fn, iters):
+        table = s_cost if fn.__name__ == "s_side" else t_cost
+        return table.get(plan.code, 9.0)
+
+    monkeypatch.setattr(autotune, "_time", fake_time)
+    res = autotune.tune_plan(plan, None, None, None, candidates=(112, 212, 22412))
+    timed = [v for v, _ in plan.set_calls[:-1]]
+    assert set(timed) == {112, 212, 22412, 32212, 1042} and len(timed) == 5
+    assert res["variant"] == 32212 and res["variant_t"] == 22412
+    assert plan.set_calls[-1] == (32212, 22412)
+
+
+def test_all_codes_are_known_to_the_library():
+    """Every default candidate is a variant code the C ABI accepts (the list
+    in fmm_api.cu, mirrored by the parity tests)."""
+    import re
+    from pathlib import Path
+    src = (Path(__file__).resolve().parents[1] / "paper_2203_07673_gb300" / "csrc"
+           / "fmm_api.cu").read_text()
+    body = src[src.index("kVariantCodes[] = {"):].split("};")[0]
+    known = {int(x) for x in re.findall(r"\d+", body.split("{", 1)[1])}
+    assert set(autotune.ALL_CODES) <= known
+    assert set(autotune.BATCH_CODES) <= known

@@ -487,3 +487,33 @@ def test_accumulating_calls_add_to_the_output(r, variant, dtype):
         err = (g - w).abs().max().item()
         assert err <= 1e-5 * max(1.0, w.abs().max().item()), err
     plan.close()
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16], ids=["f32", "bf16"])
+def test_tune_plan_on_the_gpu_keeps_results(dtype):
+    """tune_plan times candidates and the plan's own codes on its operands,
+    sets the fastest per side, and the tuned plan still matches the oracle
+    (forward, transpose and backward)."""
+    from paper_2203_07673_gb300 import autotune
+    S, _ = pattern("hubs", 13)
+    rng = np.random.default_rng(13)
+    r = 64
+    vals = rng.uniform(0.0, 1.0, S.nnz).astype(np.float32)
+    A = (rng.standard_normal((S.m, r)) / np.sqrt(r)).astype(np.float32)
+    B = (rng.standard_normal((S.n, r)) / np.sqrt(r)).astype(np.float32)
+    rp, ci, vt, At, Bt = upload(S, vals, A, B, dtype)
+    from paper_2203_07673_gb300 import fmm
+    plan = fmm.Plan(rp, ci, S.n, r, dtype, split_nnz=64)
+    G = torch.randn(S.m, r, device="cuda")
+    res = autotune.tune_plan(plan, vt, At, Bt, G, candidates=(112, 212, 32212), iters=2)
+    info = plan.info()
+    assert (info["variant"], info["variant_t"]) == (res["variant"], res["variant_t"])
+    assert res["variant"] in res["ms"] and res["variant_t"] in res["ms_t"]
+    A64, B64 = At.double().cpu().numpy(), Bt.double().cpu().numpy()
+    ref = oracle.fusedmm(S.row_ptr, S.col_idx, vals, A64, B64, S.n)
+    mag = oracle.fusedmm(S.row_ptr, S.col_idx, vals, np.abs(A64), np.abs(B64), S.n)
+    assert_close("tuned fusedmm", fmm.fusedmm(plan, vt, At, Bt), ref, mag, r, deg_max(S))
+    ref_t = oracle.fusedmm_t(S.row_ptr, S.col_idx, vals, A64, B64, S.n)
+    mag_t = oracle.fusedmm_t(S.row_ptr, S.col_idx, vals, np.abs(A64), np.abs(B64), S.n)
+    assert_close("tuned fusedmm_t", fmm.fusedmm_t(plan, vt, At, Bt), ref_t, mag_t, r, deg_max(S))
+    plan.close()
