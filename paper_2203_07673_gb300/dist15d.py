@@ -2,7 +2,7 @@
 dense-shifting, dense-replicating algorithm with local kernel fusion
 (Algorithm 1, FusedMM15D), the same grid with replication reuse instead of
 local kernel fusion (Sec. IV-B strategy (1), ReplicationReuse15D), and the
-1.5D sparse-shifting algorithm (c = 1, SparseShift15D).
+1.5D sparse-shifting, dense-replicating algorithm (SparseShift15D).
 
 The grid (Sec. V, "1.5D Dense Shifting, Dense Replicating"): p ranks form c
 layers of p/c ranks each; rank k sits in layer k // (p/c) at position
@@ -550,40 +550,57 @@ def slice_bounds(r: int, parts: int) -> np.ndarray:
 
 class SparseShift15D:
     """FusedMMA and FusedMMB by the 1.5D sparse-shifting, dense-replicating
-    algorithm (Sec. V, c = 1): the dense matrices are divided by column
-    slices of r, the sparse matrix by block rows, and the block rows circulate.
+    algorithm (Sec. V) on the (p/c) x c grid: the dense matrices are divided
+    by column slices of r, the sparse matrix by block rows, and the block
+    rows circulate within each layer.
 
-    Local kernel fusion is impossible in this layout (a rank holds only a
-    slice of every row of A and B, so no rank can finish a dot product before
-    the aggregation, Sec. IV-B), so FusedMM runs as SDDMM then SpMM: round 1
-    passes each block row's values around the ring, every rank adding its
-    slice's partial dot products (fmm_sddmm_acc); after p phases and p shifts
-    each block is back at its owner with its SDDMM values complete.  Round 2
-    passes the completed blocks around again, every rank applying each block
-    to its column slice (fmm_spmm for FusedMMA rows; fmm_spmm_t_acc, summed
-    over the blocks, for FusedMMB).  The patterns are laid out on every rank
-    once (one plan per block row, at the rank's slice width), so only the
-    values travel: nnz/p floats per shift.
+    S is cut into p block rows balanced by nonzeros; layer l owns the p/c
+    consecutive blocks l (p/c) .. (l + 1)(p/c) - 1 (rows R_l), and its p/c
+    ranks hold the p/c column slices of r.  Rank (q, l) holds slice q of A's
+    rows R_l and of B's columns C_l (B in c blocks of n / c rows); one
+    all-gather along the fiber gives it slice q of every row of B (the
+    replication, reused by both halves).  Local kernel fusion is impossible
+    in this layout (a rank holds only a slice of every row of A and B, so no
+    rank can finish a dot product before the aggregation, Sec. IV-B), so
+    FusedMM runs as SDDMM then SpMM: round 1 passes each block row's values
+    around the layer, every rank adding its slice's partial dot products
+    (fmm_sddmm_acc); after p/c phases and p/c shifts each block is back at
+    its owner with its SDDMM values complete.  Round 2 passes the completed
+    blocks around again, every rank applying each block to its slice
+    (fmm_spmm for FusedMMA rows R_l; fmm_spmm_t_acc for FusedMMB, summed over
+    the layer's blocks and then reduce-scattered along the fiber, since every
+    layer holds part of the rows of S).  The patterns are laid out on every
+    rank once (one plan per block row of its layer, at its slice width), so
+    only values travel: nnz/p floats per shift.  With c = 1 there is one
+    layer holding all rows and every rank all of B's rows.
 
     Every rank passes the whole pattern (row_ptr, col_idx: int32 on its
-    device), the values of all nonzeros (or None), its column slices A_k
-    (m x r_k) and B_k (n x r_k), and gets its slices of the outputs."""
+    device), the values of all nonzeros (or None), A_k = A[R_l, slice q]
+    and B_k = B[C_l, slice q], and gets out[R_l, slice q] (FusedMMA) and
+    out_t[C_l, slice q] (FusedMMB)."""
 
     def __init__(self, row_ptr, col_idx, n, r, dtype=torch.float32, group=None, ops=None,
-                 row_bounds=None):
-        self.grid = Grid15D(1, group)
-        self.p, self.k = self.grid.p, self.grid.k
+                 row_bounds=None, c=1):
+        self.grid = Grid15D(c, group)
+        g = self.grid
+        self.p, self.k, self.c, self.lp = g.p, g.k, g.c, g.lp
         self.n, self.r, self.dtype = int(n), int(r), dtype
         self.m = row_ptr.numel() - 1
         self.ops = ops if ops is not None else LibraryOps()
         rp_h = row_ptr.cpu().numpy()
         self.row_bounds = (row_bounds_by_nnz(rp_h, self.p) if row_bounds is None
                            else np.asarray(row_bounds, dtype=np.int64))
-        self.slices = slice_bounds(self.r, self.p)
-        self.width = int(self.slices[self.k + 1] - self.slices[self.k])
+        self.slices = slice_bounds(self.r, self.lp)
+        self.width = int(self.slices[g.q + 1] - self.slices[g.q])
         self.nnz_bounds = rp_h.astype(np.int64)[self.row_bounds]
+        # this layer's block rows and rows, and the fiber's blocks of B
+        self.b0 = g.layer * self.lp
+        self.r_lo = int(self.row_bounds[self.b0])
+        self.r_hi = int(self.row_bounds[self.b0 + self.lp])
+        self.col_bounds = col_bounds_uniform(self.n, self.c)
         self.plans = []
-        for b in range(self.p):
+        for i in range(self.lp):
+            b = self.b0 + i
             r0, r1 = int(self.row_bounds[b]), int(self.row_bounds[b + 1])
             p0, p1 = int(self.nnz_bounds[b]), int(self.nnz_bounds[b + 1])
             rp = (row_ptr[r0:r1 + 1].long() - p0).to(torch.int32)
@@ -596,7 +613,8 @@ class SparseShift15D:
         self.plans = []
 
     def block_of_phase(self, t: int) -> int:
-        return (self.k + t) % self.p
+        """The block row (global index) whose values this rank holds in phase t."""
+        return self.b0 + (self.grid.q + t) % self.lp
 
     def _rows(self, b):
         return int(self.row_bounds[b]), int(self.row_bounds[b + 1])
@@ -604,47 +622,58 @@ class SparseShift15D:
     def _nz(self, b):
         return int(self.nnz_bounds[b]), int(self.nnz_bounds[b + 1])
 
-    def _sddmm_round(self, vals, A_k, B_k):
-        """Round 1: every block row's SDDMM values, summed over the slices;
-        returns (this rank's block values, padded buffer pair, current)."""
+    def _sddmm_round(self, vals, A_k, TB):
+        """Round 1: every block row's SDDMM values, summed over the layer's
+        slices; returns (the value buffers, the current one: this rank's
+        own block, complete)."""
         g = self.grid
         dev = A_k.device
         bufs = [torch.zeros(self.maxnz, dtype=torch.float32, device=dev),
                 torch.empty(self.maxnz, dtype=torch.float32, device=dev)]
         cur = 0
-        for t in range(self.p):
+        for t in range(self.lp):
             b = self.block_of_phase(t)
             (r0, r1), (p0, p1) = self._rows(b), self._nz(b)
             v = None if vals is None else vals[p0:p1]
-            self.ops.sddmm_acc(self.plans[b], v, A_k[r0:r1], B_k, bufs[cur][:p1 - p0])
+            self.ops.sddmm_acc(self.plans[b - self.b0], v, A_k[r0 - self.r_lo:r1 - self.r_lo], TB,
+                               bufs[cur][:p1 - p0])
             g.wait(g.shift(bufs[cur], bufs[1 - cur]))
             cur = 1 - cur
         return bufs, cur
 
+    def _replicated_b(self, B_k):
+        return self.grid.gather_fiber(B_k, np.diff(self.col_bounds))
+
     def fusedmm(self, vals, A_k, B_k):
-        """This rank's column slice of FusedMMA (m x r_k)."""
+        """out[R_l, slice q] of FusedMMA ((r_hi - r_lo) x r_q)."""
         g = self.grid
-        bufs, cur = self._sddmm_round(vals, A_k, B_k)
-        out = torch.empty((self.m, self.width), dtype=torch.float32, device=A_k.device)
-        for t in range(self.p):
+        TB = self._replicated_b(B_k)
+        bufs, cur = self._sddmm_round(vals, A_k, TB)
+        out = torch.empty((self.r_hi - self.r_lo, self.width), dtype=torch.float32,
+                          device=A_k.device)
+        for t in range(self.lp):
             b = self.block_of_phase(t)
             (r0, r1), (p0, p1) = self._rows(b), self._nz(b)
-            pend = g.shift(bufs[cur], bufs[1 - cur]) if t + 1 < self.p else []
-            self.ops.spmm(self.plans[b], bufs[cur][:p1 - p0], B_k, out[r0:r1])
+            pend = g.shift(bufs[cur], bufs[1 - cur]) if t + 1 < self.lp else []
+            self.ops.spmm(self.plans[b - self.b0], bufs[cur][:p1 - p0], TB,
+                          out[r0 - self.r_lo:r1 - self.r_lo])
             g.wait(pend)
             cur = 1 - cur
         return out
 
     def fusedmm_t(self, vals, A_k, B_k):
-        """This rank's column slice of FusedMMB (n x r_k)."""
+        """out_t[C_l, slice q] of FusedMMB."""
         g = self.grid
-        bufs, cur = self._sddmm_round(vals, A_k, B_k)
-        out = torch.zeros((self.n, self.width), dtype=torch.float32, device=A_k.device)
-        for t in range(self.p):
+        TB = self._replicated_b(B_k)
+        bufs, cur = self._sddmm_round(vals, A_k, TB)
+        part = torch.zeros((self.n, self.width), dtype=torch.float32, device=A_k.device)
+        for t in range(self.lp):
             b = self.block_of_phase(t)
             (r0, r1), (p0, p1) = self._rows(b), self._nz(b)
-            pend = g.shift(bufs[cur], bufs[1 - cur]) if t + 1 < self.p else []
-            self.ops.spmm_t_acc(self.plans[b], bufs[cur][:p1 - p0], A_k[r0:r1], out)
+            pend = g.shift(bufs[cur], bufs[1 - cur]) if t + 1 < self.lp else []
+            self.ops.spmm_t_acc(self.plans[b - self.b0], bufs[cur][:p1 - p0],
+                                A_k[r0 - self.r_lo:r1 - self.r_lo], part)
             g.wait(pend)
             cur = 1 - cur
-        return out
+        # every layer summed its rows: the sum over the fiber, scattered
+        return g.reduce_scatter_fiber(part, self.col_bounds)

@@ -181,30 +181,37 @@ def reuse_rank_main(rank, world, port, out, seed, r, use_gpu, vals_none, c=1):
         dist.destroy_process_group()
 
 
-def sparse_rank_main(rank, world, port, out, seed, r, use_gpu, vals_none):
-    """The sparse-shifting algorithm: every rank holds the whole pattern and
-    values and its column slices of A and B; returns its output slices."""
+def sparse_rank_main(rank, world, port, out, seed, r, use_gpu, vals_none, c=1):
+    """The sparse-shifting algorithm on the (world/c) x c grid: every rank
+    holds the whole pattern and values, A[R_l, slice q] and B[C_l, slice q];
+    returns out[R_l, slice q] and out_t[C_l, slice q]."""
     import torch.distributed as dist
     from paper_2203_07673_gb300 import dist15d
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
         S, vals, A, B, G = problem(seed, r=r)
-        sl = dist15d.slice_bounds(r, world)
-        j0, j1 = int(sl[rank]), int(sl[rank + 1])
+        lp = world // c
+        layer, q = divmod(rank, lp)
+        sl = dist15d.slice_bounds(r, lp)
+        j0, j1 = int(sl[q]), int(sl[q + 1])
+        rb = dist15d.row_bounds_by_nnz(S.row_ptr, world)
+        r0, r1 = int(rb[layer * lp]), int(rb[(layer + 1) * lp])
+        cb = dist15d.col_bounds_uniform(S.n, c)
+        c0, c1 = int(cb[layer]), int(cb[layer + 1])
         dev = torch.device("cuda", 0) if use_gpu else torch.device("cpu")
         rp = torch.from_numpy(S.row_ptr.copy()).to(dev)
         ci = torch.from_numpy(S.col_idx.copy()).to(dev)
         vt = None if vals_none else torch.from_numpy(vals).to(dev)
-        Ak = torch.from_numpy(np.ascontiguousarray(A[:, j0:j1])).to(dev)
-        Bk = torch.from_numpy(np.ascontiguousarray(B[:, j0:j1])).to(dev)
+        Ak = torch.from_numpy(np.ascontiguousarray(A[r0:r1, j0:j1])).to(dev)
+        Bk = torch.from_numpy(np.ascontiguousarray(B[c0:c1, j0:j1])).to(dev)
         ops = None if use_gpu else OracleOps()
-        d = dist15d.SparseShift15D(rp, ci, S.n, r, torch.float32, ops=ops)
+        d = dist15d.SparseShift15D(rp, ci, S.n, r, torch.float32, ops=ops, c=c)
         res = dict(out=d.fusedmm(vt, Ak, Bk), out_t=d.fusedmm_t(vt, Ak, Bk))
         if use_gpu:
             torch.cuda.synchronize()
         out[rank] = {k: v.cpu().numpy() for k, v in res.items()}
-        out[f"slice{rank}"] = (j0, j1)
+        out[f"slice{rank}"] = (j0, j1, r0, r1, c0, c1)
         d.close()
         dist.barrier()
     finally:

@@ -219,20 +219,29 @@ def test_one_rank_without_a_process_group():
 
 
 def assemble_slices(res, world, S, r):
+    """Every rank's (rows, column slice) blocks into whole matrices; every
+    element must come from exactly one rank."""
     out = np.zeros((S.m, r)); out_t = np.zeros((S.n, r))
+    seen, seen_t = np.zeros((S.m, r), int), np.zeros((S.n, r), int)
     for k in range(world):
-        j0, j1 = res[f"slice{k}"]
-        out[:, j0:j1] = res[k]["out"]; out_t[:, j0:j1] = res[k]["out_t"]
+        j0, j1, r0, r1, c0, c1 = res[f"slice{k}"]
+        out[r0:r1, j0:j1] = res[k]["out"]; out_t[c0:c1, j0:j1] = res[k]["out_t"]
+        seen[r0:r1, j0:j1] += 1; seen_t[c0:c1, j0:j1] += 1
+    assert np.all(seen == 1) and np.all(seen_t == 1)
     return out, out_t
 
 
-@pytest.mark.parametrize("world", [2, 3])
+@pytest.mark.parametrize("world,c", [(2, 1), (3, 1), (2, 2), (4, 2), (4, 4)])
 @pytest.mark.parametrize("vals_none", [False, True])
-def test_sparse_shifting_matches_the_whole_matrix(world, vals_none):
+def test_sparse_shifting_matches_the_whole_matrix(world, c, vals_none):
+    """Sparse shifting on the (world/c) x c grid: block rows circulate in
+    each layer, B is all-gathered along the fiber, FusedMMB reduce-scattered
+    along it."""
     import dist15d_ranks
-    seed, r = 31 + world, 9
+    seed, r = 31 + world + c, 9
     S, vals, A, B, G = dist15d_ranks.problem(seed, r=r)
-    res = run_ranks(world, seed, r, use_gpu=False, vals_none=vals_none, body="sparse_rank_main")
+    res = run_ranks(world, seed, r, use_gpu=False, vals_none=vals_none, body="sparse_rank_main",
+                    c=c)
     got = assemble_slices(res, world, S, r)
     want = expected(S, None if vals_none else vals, A, B, G)[:2]
     for name, x, y in zip(("out", "out_t"), got, want):

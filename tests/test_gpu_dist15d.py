@@ -124,3 +124,18 @@ def test_replicated_grid_bf16_on_one_gpu():
     for name, x, y in zip(("out", "out_t", "dA", "dB", "ds"), got, want):
         assert np.all(np.isfinite(x)), name
         assert rel(x, y) <= 1e-5, name
+
+
+def test_sparse_shifting_replicated_grid_on_one_gpu():
+    """Sparse shifting on a 2 x 2 grid with the library's kernels: B
+    all-gathered along each fiber, block rows circulating in each layer,
+    FusedMMB reduce-scattered along the fiber."""
+    import dist15d_ranks
+    seed, r = 97, 64
+    S, vals, A, B, G = dist15d_ranks.problem(seed, r=r)
+    res = run_ranks(4, seed, r, use_gpu=True, body="sparse_rank_main", c=2)
+    got = assemble_slices(res, 4, S, r)
+    want = expected(S, vals, A, B, G)[:2]
+    for name, x, y in zip(("out", "out_t"), got, want):
+        assert np.all(np.isfinite(x)), name
+        assert rel(x, y) <= 1e-5, name
