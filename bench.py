@@ -449,15 +449,29 @@ def cusparse_forward(rp, ci, vals, A, B, S, r, fused_out, timed):
         return {"unavailable": f"{type(ex).__name__}: {str(ex).splitlines()[0][:160]}"}
 
 
+def l2_cache_bytes():
+    """The L2 size of the current CUDA device (queried), else GB300's 126 MiB."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.get_device_properties(torch.cuda.current_device()).L2_cache_size)
+    except Exception:
+        pass
+    return 126 << 20
+
+
 def workload_config(w, args):
     S = w["S"]
     step = ("FusedMMA forward + backward (dA, dB, ds); units = nnz*r per step"
             if args.workload == 3 else "FusedMMA + FusedMMB; units = 2*nnz*r per step")
+    e = 4 if w["dtype"] == "f32" else 2
+    l2 = l2_cache_bytes()
+    dense = (S.m + S.n) * w["r"] * e
     return {"workload": w["name"], "m": S.m, "n": S.n, "nnz": S.nnz, "r": w["r"],
             "input_dtype": w["dtype"], "step": step,
-            "l2": "not flushed: A and B are larger than L2" if S.m * w["r"] * 4 > 2**28
-            else "L2-resident inputs", "parallelism": f"replicas x{args.gpus}",
-            "scale_rows": args.scale}
+            "l2": ("not flushed: A and B are larger than L2" if dense > 2 * l2
+                   else "L2-resident inputs"),
+            "parallelism": f"replicas x{args.gpus}", "scale_rows": args.scale}
 
 
 # ------------------------------------------------------------------ GPU leg
